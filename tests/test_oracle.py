@@ -1,0 +1,379 @@
+"""Pins for the CPU oracle: it is checked against things other than itself.
+
+Forward substitution: library triangular solves, b = L x_true recovery, closed forms.
+Level sets: brute-force longest paths on tiny DAGs, the grid's closed form r + c.
+Rewriting: the worked example of Section II.B / Fig. 2, the elimination identity
+L' = E L (a dense matrix product), the grid's binomial closed form, and x' = x.
+Planner: the costMap example of Section III with the paper's costs injected.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+from paper_2206_05843_gb300 import synth as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_random_lower(n, density, seed, dominant=True):
+    rng = np.random.default_rng(seed)
+    counts, cols = [], []
+    for i in range(n):
+        c = np.nonzero(rng.random(i) < density)[0]
+        counts.append(len(c))
+        cols.extend(c.tolist())
+    m = S.gen_from_deps(n, np.array(counts), np.array(cols, dtype=np.int64), S.rng_for(seed))
+    if not dominant:
+        rp = m.rowptr.astype(np.int64)
+        m.vals[rp[1:] - 1] = rng.uniform(0.5, 2.0, n) * rng.choice([-1, 1], n)
+    return m
+
+
+# ---------------------------------------------------------------------------------
+# Algorithm 1
+# ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("n", [1, 7, 33, 64])
+def test_forward_subst_matches_library_triangular_solve(n, seed):
+    m = small_random_lower(n, 0.3, seed, dominant=(seed % 2 == 0))
+    L = m.to_dense()
+    b = np.random.default_rng(seed + 100).uniform(-1, 1, size=(3, n))
+    x = O.forward_subst(m.rowptr, m.colidx, m.vals, b)
+    ref = scipy.linalg.solve_triangular(L, b.T, lower=True).T
+    ref2 = np.linalg.solve(L, b.T).T
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(x - ref).max() <= 1e-12 * scale
+    assert np.abs(x - ref2).max() <= 1e-9 * scale
+
+
+def test_forward_subst_recovers_x_true_config0():
+    m, b, xt = S.gen_config("c0")
+    x = O.forward_subst(m.rowptr, m.colidx, m.vals, b)
+    assert np.linalg.norm(x - xt) / np.linalg.norm(xt) < 1e-14
+
+
+def test_forward_subst_closed_forms():
+    n = 50
+    rng = np.random.default_rng(3)
+    b = rng.uniform(-1, 1, n)
+    # identity
+    ident = S.gen_from_deps(n, np.zeros(n, np.int64), np.zeros(0, np.int64), None, diag=1.0)
+    assert np.array_equal(O.forward_subst(ident.rowptr, ident.colidx, ident.vals, b), b)
+    # diagonal
+    d = rng.uniform(0.5, 3.0, n)
+    diag = S.gen_from_deps(n, np.zeros(n, np.int64), np.zeros(0, np.int64), None, diag=d)
+    assert np.allclose(O.forward_subst(diag.rowptr, diag.colidx, diag.vals, b), b / d, rtol=1e-15, atol=0)
+    # bidiagonal: x_i - a x_{i-1} = b_i  ->  x_i = sum_{k<=i} a^{i-k} b_k
+    a = 0.7
+    counts = np.array([0] + [1] * (n - 1))
+    cols = np.arange(n - 1)
+    bi = S.gen_from_deps(n, counts, cols, None, offdiag=-a, diag=1.0)
+    x = O.forward_subst(bi.rowptr, bi.colidx, bi.vals, b)
+    closed = np.array([sum(a ** (i - k) * b[k] for k in range(i + 1)) for i in range(n)])
+    assert np.allclose(x, closed, rtol=1e-12, atol=1e-13)
+
+
+def test_validate_codes():
+    m = small_random_lower(10, 0.4, 0)
+    assert O.validate(m.rowptr, m.colidx, m.vals) == (0, -1)
+    v = m.vals.copy()
+    v[m.rowptr[4] + (m.rowptr[5] - m.rowptr[4]) - 1] = 0.0
+    assert O.validate(m.rowptr, m.colidx, v) == (5, 4)
+    c = m.colidx.copy()
+    c[m.rowptr[6] - 1] = 2  # diagonal of row 5 replaced
+    code, row = O.validate(m.rowptr, c, m.vals)
+    assert code in (3, 4) and row == 5
+
+
+# ---------------------------------------------------------------------------------
+# level sets
+# ---------------------------------------------------------------------------------
+
+def brute_levels(n, deps):
+    """Longest path (in edges) ending at each node, by enumerating every path."""
+    best = [0] * n
+    preds = {i: deps[i] for i in range(n)}
+    # enumerate all paths backwards from every node
+    for end in range(n):
+        stack = [(end, 0)]
+        while stack:
+            node, length = stack.pop()
+            if length > best[end]:
+                best[end] = length
+            for p in preds[node]:
+                stack.append((p, length + 1))
+    return best
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_levels_brute_force_longest_path(seed):
+    n = 12
+    m = small_random_lower(n, 0.35, seed)
+    rp = m.rowptr.astype(np.int64)
+    deps = {i: m.colidx[rp[i]:rp[i + 1] - 1].tolist() for i in range(n)}
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    assert lev.tolist() == brute_levels(n, deps)
+    assert mm == max(brute_levels(n, deps)) + 1
+
+
+def test_levels_networkx_critical_path():
+    nx = pytest.importorskip("networkx")
+    m = small_random_lower(200, 0.05, 11)
+    rp = m.rowptr.astype(np.int64)
+    g = nx.DiGraph()
+    g.add_nodes_from(range(m.n))
+    for i in range(m.n):
+        for j in m.colidx[rp[i]:rp[i + 1] - 1]:
+            g.add_edge(int(j), i)
+    _, mm = O.levels(m.rowptr, m.colidx)
+    assert mm == nx.dag_longest_path_length(g) + 1
+
+
+@pytest.mark.parametrize("side", [1, 2, 5, 17, 64])
+def test_levels_laplacian_closed_form(side):
+    m = S.gen_laplacian(side)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    r, c = np.divmod(np.arange(m.n), side)
+    assert np.array_equal(lev, r + c)
+    assert mm == 2 * side - 1
+    st = O.level_stats(m.rowptr, lev, mm)
+    ell = np.arange(mm)
+    assert np.array_equal(st["rows"], np.minimum(ell + 1, 2 * side - 1 - ell))
+    # cost of a level is 2 * sum(nnz) - rows (Section III)
+    assert st["cost"].sum() == 2 * m.nnz - m.n
+
+
+def test_levels_redblack_two_levels():
+    m = S.gen_redblack(16)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    assert mm == 2 and (lev == 0).sum() == 128
+
+
+def test_levels_layered():
+    m = S.gen_layered(5, 300, 2)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    assert mm == 5 and np.array_equal(lev, np.arange(m.n) // 300)
+
+
+# ---------------------------------------------------------------------------------
+# rewriting (Section II.B)
+# ---------------------------------------------------------------------------------
+
+def fig2_matrix(seed=0):
+    g = json.load(open(os.path.join(GOLD, "fig2_worked_example.json")))
+    n = g["n"]
+    counts = np.array([len(g["deps"][str(i)]) for i in range(n)])
+    cols = np.array([c for i in range(n) for c in g["deps"][str(i)]], dtype=np.int64)
+    rng = np.random.default_rng(seed)
+    off = rng.uniform(-2, 2, cols.size)
+    diag = rng.uniform(0.5, 2.0, n)
+    return g, S.gen_from_deps(n, counts, cols, None, offdiag=off, diag=diag)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_rewrite_worked_example_closed_form(seed):
+    g, m = fig2_matrix(seed)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    assert lev.tolist() == g["levels_before"]
+    L = m.to_dense()
+    b = np.random.default_rng(seed + 9).uniform(-1, 1, 4)
+    # twice: x3 = (b3 - L31 * ((b1 - L10 * (b0 / L00)) / L11)) / L33
+    tgt = lev.copy()
+    tgt[3] = g["rewrite_twice"]["target_level"]
+    sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, tgt)
+    assert sy.ccol[sy.cptr[3]:sy.cptr[4]].tolist() == g["rewrite_twice"]["deps_after"]
+    x3 = (b[3] - L[3, 1] * ((b[1] - L[1, 0] * (b[0] / L[0, 0])) / L[1, 1])) / L[3, 3]
+    assert sy.solve(b)[3] == pytest.approx(x3, rel=1e-14, abs=1e-15)
+    # rearranged: b'_3 = sum_m e_3m b_m with the constants folded; dval = 1 (no division)
+    e = dict(zip(sy.ecol[sy.eptr[3]:sy.eptr[4]].tolist(), sy.eval[sy.eptr[3]:sy.eptr[4]].tolist()))
+    assert sy.dval[3] == 1.0
+    assert e[3] == pytest.approx(1 / L[3, 3], rel=1e-15)
+    assert e[1] == pytest.approx(-L[3, 1] / (L[1, 1] * L[3, 3]), rel=1e-14)
+    assert e[0] == pytest.approx(L[3, 1] * L[1, 0] / (L[0, 0] * L[1, 1] * L[3, 3]), rel=1e-14)
+    # once (middle graph of Fig. 2): row 3 now depends on row 0
+    tgt = lev.copy()
+    tgt[3] = g["rewrite_once"]["target_level"]
+    sy1 = O.rewrite(m.rowptr, m.colidx, m.vals, lev, tgt)
+    assert sy1.ccol[sy1.cptr[3]:sy1.cptr[4]].tolist() == g["rewrite_once"]["deps_after"]
+    c30 = sy1.cval[sy1.cptr[3]]
+    # x3 = (b3 - L31 (b1 - L10 x0) / L11) / L33  ->  coefficient of x0 is -L31 L10 / (L11 L33)
+    assert -c30 == pytest.approx(L[3, 1] * L[1, 0] / (L[1, 1] * L[3, 3]), rel=1e-14)
+    l2, m2 = sy1.levels()
+    assert l2[3] == 1 and m2 == 2
+
+
+def dense_system(sy: O.System, n):
+    """Rows of the rewritten equations as dense [A | F] with A x = F b."""
+    A = np.zeros((n, n))
+    F = np.zeros((n, n))
+    for r in range(n):
+        A[r, r] = sy.dval[r]
+        A[r, sy.ccol[sy.cptr[r]:sy.cptr[r + 1]]] += sy.cval[sy.cptr[r]:sy.cptr[r + 1]]
+        if sy.moved[r]:
+            F[r, sy.ecol[sy.eptr[r]:sy.eptr[r + 1]]] = sy.eval[sy.eptr[r]:sy.eptr[r + 1]]
+        else:
+            F[r, r] = 1.0
+    return A, F
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("kind,k", [(O.DEPTH, 1), (O.DEPTH, 3), (O.NAIVE, 0)])
+def test_rewrite_is_elimination_E_times_L(seed, kind, k):
+    """Every rewritten row is a combination of original rows: A = F L, where the columns
+    the rewrite removed become (numerically) zero."""
+    m = small_random_lower(60, 0.08, seed)
+    L = m.to_dense()
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    p = O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k)
+    sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, p.target)
+    A, F = dense_system(sy, m.n)
+    assert np.allclose(F @ L, A, rtol=0, atol=1e-13)
+    # no dependency on a row of the same or a later level after re-levelling
+    l2, m2 = sy.levels()
+    for r in range(m.n):
+        deps = sy.ccol[sy.cptr[r]:sy.cptr[r + 1]]
+        assert np.all(l2[deps] < l2[r])
+        if sy.moved[r]:
+            assert np.all(p.target[deps] < p.target[r])
+    assert m2 <= p.levels_after <= mm
+    b = np.random.default_rng(seed).uniform(-1, 1, (2, m.n))
+    assert np.allclose(sy.solve(b), O.forward_subst(m.rowptr, m.colidx, m.vals, b), rtol=0, atol=1e-13)
+    # dominant input: rearranged coefficients stay below one in magnitude
+    assert np.abs(sy.cval[np.repeat(sy.moved.astype(bool), np.diff(sy.cptr))]).max(initial=0) < 1
+    assert np.abs(sy.eval).max(initial=0) <= 1
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_rewrite_laplacian_binomial_closed_form(k):
+    """Grid rows at depth d inside a group: x = sum over the cone of b with weight
+    C(e, a) / 4^(e+1) at distance e, minus the d+2 points one level above the target with
+    weight C(d+1, a) / 4^(d+1) (each step back goes up or left with weight 1/4)."""
+    side = 14
+    m = S.gen_laplacian(side)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    p = O.plan(m.rowptr, m.colidx, lev, mm, O.DEPTH, k=k)
+    sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, p.target)
+    checked = 0
+    for idx in range(m.n):
+        r, c = divmod(idx, side)
+        d = lev[idx] - p.target[idx]
+        if d == 0 or r < d + 2 or c < d + 2:
+            continue  # unmoved or touching the boundary
+        cdict = dict(zip(sy.ccol[sy.cptr[idx]:sy.cptr[idx + 1]].tolist(),
+                         sy.cval[sy.cptr[idx]:sy.cptr[idx + 1]].tolist()))
+        want_c = {(r - a) * side + (c - (d + 1 - a)): -math.comb(d + 1, a) / 4 ** (d + 1) for a in range(d + 2)}
+        assert set(cdict) == set(want_c)
+        for key, v in want_c.items():
+            assert cdict[key] == pytest.approx(v, rel=1e-14)
+        edict = dict(zip(sy.ecol[sy.eptr[idx]:sy.eptr[idx + 1]].tolist(),
+                         sy.eval[sy.eptr[idx]:sy.eptr[idx + 1]].tolist()))
+        want_e = {}
+        for e in range(d + 1):
+            for a in range(e + 1):
+                want_e[(r - a) * side + (c - (e - a))] = math.comb(e, a) / 4 ** (e + 1)
+        assert set(edict) == set(want_e)
+        for key, v in want_e.items():
+            assert edict[key] == pytest.approx(v, rel=1e-14)
+        checked += 1
+    assert checked > 20
+
+
+def test_rewrite_far_with_tiny_pivots_blows_up():
+    """Fig. 3: rewriting far over rows with small pivots produces huge constants."""
+    n = 12
+    counts = np.array([0] + [1] * (n - 1))
+    cols = np.arange(n - 1)
+    m = S.gen_from_deps(n, counts, cols, None, offdiag=1.0, diag=1e-3)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    tgt = np.zeros(n, np.int32)
+    sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, tgt)
+    assert np.abs(sy.eval).max() > 1e30
+
+
+# ---------------------------------------------------------------------------------
+# the planner (Section III)
+# ---------------------------------------------------------------------------------
+
+def test_planner_costmap_example():
+    g = json.load(open(os.path.join(GOLD, "costmap_example.json")))
+    # structure giving the example's levels and original costs (2 nnz -> 3, 3 nnz -> 5)
+    deps = {0: [], 1: [], 2: [0], 3: [1], 4: [2], 5: [2, 3], 6: [4], 7: [5]}
+    n = 8
+    counts = np.array([len(deps[i]) for i in range(n)])
+    cols = np.array([c for i in range(n) for c in deps[i]], dtype=np.int64)
+    m = S.gen_from_deps(n, counts, cols, S.rng_for(0))
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    assert [sorted(np.nonzero(lev == l)[0].tolist()) for l in range(mm)] == g["levels"]
+    st = O.level_stats(m.rowptr, lev, mm)
+    oc = g["original_row_cost"]
+    assert [int(v) for v in st["cost"]] == [sum(oc[str(r)] for r in rows) for rows in g["levels"]]
+    inj = np.array([g["cost_on_target"].get(str(i), g["original_row_cost"][str(i)]) for i in range(n)])
+    p = O.plan(m.rowptr, m.colidx, lev, mm, O.NAIVE, avg=g["avg_level_cost"], injected_cost=inj)
+    assert p.target.tolist() == [g["expected_target"][str(i)] for i in range(n)]
+    for lvl, cost in g["expected_level_cost"].items():
+        assert int(p.row_cost[p.target == int(lvl)].sum()) == cost
+    assert mm - p.levels_after == g["expected_levels_removed"]
+
+
+def test_planner_naive_fat_level_breaks_run_and_avg_is_fixed():
+    # chain of single rows with one very wide level in the middle
+    n_chain = 6
+    counts, cols = [], []
+    for i in range(n_chain):
+        counts.append(1 if i else 0)
+        cols.extend([i - 1] if i else [])
+    wide = 40
+    for w in range(wide):
+        counts.append(1)
+        cols.append(n_chain - 1)
+    base = n_chain + wide
+    for i in range(base, base + n_chain):
+        counts.append(1)
+        cols.append(i - 1 if i > base else n_chain + wide - 1)
+    n = base + n_chain
+    m = S.gen_from_deps(n, np.array(counts), np.array(cols, dtype=np.int64), S.rng_for(1))
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    p = O.plan(m.rowptr, m.colidx, lev, mm, O.NAIVE)
+    st = O.level_stats(m.rowptr, lev, mm)
+    assert p.avg == pytest.approx(st["cost"].sum() / mm, abs=1e-6)
+    wide_level = lev[n_chain]
+    assert np.all(p.target[n_chain:base] == wide_level)  # fat level keeps its rows
+    assert np.all(p.target[:n_chain] < wide_level)
+    assert np.all(p.target[base:] > wide_level)
+    assert p.levels_after < mm
+
+
+def test_planner_depth_k_group_counts():
+    m = S.gen_laplacian(32)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    for k in (1, 2, 4):
+        p = O.plan(m.rowptr, m.colidx, lev, mm, O.DEPTH, k=k)
+        assert p.levels_after == math.ceil(mm / (k + 1))
+        assert np.array_equal(p.target, lev - lev % (k + 1))
+
+
+def test_planner_nnz_cap_is_respected():
+    m, b, _ = S.gen_config("c1", scale=0.01)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    for cap in (1.05, 1.2, 1.5):
+        p = O.plan(m.rowptr, m.colidx, lev, mm, O.NAIVE, cap=cap)
+        assert p.stored_nnz <= math.floor(cap * p.nnz_l)
+        sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, p.target)
+        stored = int(sy.cptr[-1]) + m.n + int(sy.eptr[-1])
+        assert stored == p.stored_nnz  # planner bookkeeping equals the rewrite's structure
+
+
+def test_planner_chosen_depths_equal_depth_k():
+    m = S.gen_laplacian(20)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    p1 = O.plan(m.rowptr, m.colidx, lev, mm, O.DEPTH, k=3)
+    p2 = O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN, depth_of_target=np.full(mm, 3))
+    assert np.array_equal(p1.target, p2.target)
+    p0 = O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN, depth_of_target=np.zeros(mm))
+    assert np.array_equal(p0.target, lev)
