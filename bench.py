@@ -1,0 +1,399 @@
+"""Benchmark: SpTRSV solve time (us) and HBM GB/s, float64, one GB300.
+
+Workload (N=1): the skewed n = 1,000,000 lower-triangular matrix (800,000 head rows with
+8 dependencies uniform over all earlier rows, a 200,000-row tail with 3 dependencies in
+the previous 4 rows), b = L x_true, one right-hand side.  The headline value is the
+solve time of the rewritten system (learned depth picker when a trained picker file is
+present, else the paper's naive avgLevelCost strategy with the nnz growth capped at 1.5x);
+the plain level-set solve of the same matrix is measured beside it.
+
+A step is one solve.  Analysis and rewriting are preprocessing: they run once before the
+timed region and their times are reported separately.  The working set (about 120 MB) is
+close to the L2 size, so L2 is flushed (a 512 MB write) before every timed solve, outside
+the event pair that times the solve.
+
+--impl reference times the CPU oracle (serial float64 forward substitution) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SpTRSV solve µs & HBM GB/s (FP64, 1 GB300): learned-rewrite vs plain level-set"
+WORKLOAD = "skewed n=1,000,000 (head 800,000 rows x 8 deps over all earlier rows; tail 200,000 rows x 3 deps in [i-4,i)), FP64, 1 RHS"
+PICKER_FILE = os.path.join(ROOT, "paper_2206_05843_gb300", "picker_trained.bin")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c2r16", "w1", "w2"])
+    ap.add_argument("--strategy", default="auto", choices=["auto", "naive", "learned", "depth1", "depth2", "depth4"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------
+
+def make_workload(name):
+    from paper_2206_05843_gb300 import synth as S
+    m, b, xt = S.gen_config(name)
+    return m, b, xt
+
+
+def alg_bytes(info: dict, n: int, nrhs: int, v: int = 8) -> int:
+    """Algorithmic bytes of one solve: row pointers, (col, value) of every stored
+    coefficient, the diagonal, the E rows of rewritten rows, b read once and x written
+    once (dependency gathers of x assumed to hit L2)."""
+    nnz_lprime = info["nnz_c"] + n  # off-diagonal coefficients + diagonal
+    rw = info["rows_moved"]
+    e = info["nnz_e"]
+    by = 4 * (n + 1) + (4 + v) * nnz_lprime + 2 * v * n * nrhs
+    if info["rewritten"] and rw:
+        by += 4 * (rw + 1) + (4 + v) * e
+    return int(by)
+
+
+# ------------------------------------------------------------------------------------
+# the reference arm: the CPU oracle
+# ------------------------------------------------------------------------------------
+
+def cpu_oracle_time(m, b, seconds: float, steps: int | None = None):
+    import oracle as O
+    O.build()
+    t_all = []
+    t0 = time.perf_counter()
+    count = 0
+    while True:
+        s = time.perf_counter()
+        O.forward_subst(m.rowptr, m.colidx, m.vals, b)
+        t_all.append(time.perf_counter() - s)
+        count += 1
+        if steps is not None and count >= steps:
+            break
+        if steps is None and time.perf_counter() - t0 > seconds:
+            break
+    return statistics.median(t_all) * 1e6, count
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    m, b, _ = make_workload(args.workload)
+    for _ in range(max(0, args.warmup)):
+        pass
+    # each step one whole oracle solve of the workload
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        O.forward_subst(m.rowptr, m.colidx, m.vals, b)
+    t0 = time.perf_counter()
+    times = []
+    for _ in range(args.steps):
+        s = time.perf_counter()
+        O.forward_subst(m.rowptr, m.colidx, m.vals, b)
+        times.append(time.perf_counter() - s)
+    total = time.perf_counter() - t0
+    us = statistics.median(times) * 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(us, 3), "unit": "us", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / max(args.steps, 1) * 1e3, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "c1" else args.workload, "solver": "CPU oracle, serial"},
+        "cpu_baseline": {"value": round(us, 3), "unit": "us", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} whole solves of the workload, median"},
+        "e2e": {"value": round(us, 3), "unit": "us", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------
+
+def build_systems(B, M, lv, strategy: str):
+    plain = B.System(M, lv)
+    kw = {}
+    used = strategy
+    if strategy in ("auto", "learned"):
+        if os.path.exists(PICKER_FILE):
+            try:
+                pk = B.Picker.load(PICKER_FILE)
+                kw = dict(kind=B.LEARNED, cap=1.5, picker=pk)
+                used = "learned"
+            except Exception as e:  # a picker that does not load: the paper's strategy
+                print(f"[bench] picker not loaded ({e}); using the naive strategy", file=sys.stderr)
+                kw = dict(kind=B.NAIVE, cap=1.5)
+                used = "naive"
+        else:
+            kw = dict(kind=B.NAIVE, cap=1.5)
+            used = "naive"
+    elif strategy == "naive":
+        kw = dict(kind=B.NAIVE, cap=1.5)
+    elif strategy.startswith("depth"):
+        kw = dict(kind=B.DEPTH_K, k=int(strategy[5:]))
+    rw = B.System(M, lv, **kw)
+    return plain, rw, used
+
+
+def time_solves(torch, sysm, bt, xt, steps, warmup, flush, stream):
+    for _ in range(warmup):
+        sysm.solve(bt, xt)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        sysm.solve(bt, xt)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return ms, wall
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2206_05843_gb300 import binding as B
+    m, b, xt_true = make_workload(args.workload)
+    nrhs = b.shape[0]
+    stream = torch.cuda.current_stream()
+    M = B.Matrix.from_host(m)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    lv = B.Levels(M)
+    torch.cuda.synchronize()
+    analyse_ms = (time.perf_counter() - t) * 1e3
+    t = time.perf_counter()
+    plain, rw, used = build_systems(B, M, lv, args.strategy)
+    torch.cuda.synchronize()
+    prep_ms = (time.perf_counter() - t) * 1e3
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    xp = torch.empty_like(bt)
+    xr = torch.empty_like(bt)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # correctness of both solves before timing (relative L2 against x_true)
+    for s, x in ((plain, xp), (rw, xr)):
+        s.solve(bt, x, check_status=True)
+    xt_ref = xt_true if xt_true is not None else None
+    errs = {}
+    if xt_ref is not None:
+        for nm, x in (("plain", xp), ("rewritten", xr)):
+            xx = x.cpu().numpy()
+            errs[nm] = float(np.linalg.norm(xx - xt_ref) / np.linalg.norm(xt_ref))
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    torch.cuda.synchronize()
+    region0 = time.perf_counter()
+    ms_plain, _ = time_solves(torch, plain, bt, xp, args.steps, args.warmup, flush, stream)
+    ms_rw, wall_rw = time_solves(torch, rw, bt, xr, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    for s in (plain, rw):
+        s.status()
+    us_plain = statistics.mean(ms_plain) * 1e3
+    us_rw = statistics.mean(ms_rw) * 1e3
+    # end to end through the public API: pinned host b -> device, solve, device -> host x
+    hb = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    db = torch.empty_like(bt)
+    for _ in range(args.warmup):
+        db.copy_(hb, non_blocking=True)
+        rw.solve(db, xr)
+        hx.copy_(xr, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        db.copy_(hb, non_blocking=True)
+        rw.solve(db, xr)
+        hx.copy_(xr, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    us_e2e = statistics.mean(e2e_ms) * 1e3
+    if world > 1:
+        t = torch.tensor([us_rw, us_plain, us_e2e], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        us_rw, us_plain, us_e2e = [float(v) for v in t.tolist()]
+    if rank != 0:
+        return 0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    info_rw = rw.refresh()
+    info_pl = plain.refresh()
+    by_rw = alg_bytes(info_rw, m.n, nrhs)
+    by_pl = alg_bytes(info_pl, m.n, nrhs)
+    gbs_rw = by_rw / (us_rw * 1e-6) / 1e9
+    gbs_pl = by_pl / (us_plain * 1e-6) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(used)
+        except (OSError, ValueError):
+            traffic = None
+    cpu = None
+    if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
+        us_cpu, count = cpu_oracle_time(m, b, args.cpu_seconds)
+        cpu = {"value": round(us_cpu, 1), "unit": "us", "cores": 1, "kind": "oracle",
+               "sample": f"{count} whole serial solves of the same workload (median), {os.cpu_count()} host cores present"}
+    line = {
+        "metric": METRIC,
+        "value": round(us_rw, 3),
+        "unit": "us",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(wall_rw / args.steps * 1e3, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD if args.workload == "c1" else args.workload,
+            "strategy": used if used != "auto" else "naive",
+            "nnz_cap": 1.5,
+            "plain_us": round(us_plain, 3),
+            "rewritten_us": round(us_rw, 3),
+            "speedup_vs_plain": round(us_plain / us_rw, 3),
+            "levels_plain": int(info_pl["m"]),
+            "levels_rewritten": int(info_rw["m"]),
+            "rows_moved": int(info_rw["rows_moved"]),
+            "stored_nnz_ratio": round(info_rw["stored_nnz"] / info_rw["nnz_l"], 4),
+            "plain_hbm_gbs": round(gbs_pl, 2),
+            "rewritten_hbm_gbs": round(gbs_rw, 2),
+            "analyse_ms": round(analyse_ms, 2),
+            "plain_and_rewrite_build_ms": round(prep_ms, 2),
+            "rel_err_vs_x_true": errs,
+            "l2": "flushed (512 MB write) before every timed solve, outside the timed events",
+            "parallelism": "replicas" if world > 1 else "1 GPU",
+        },
+        "roofline": {"bound": "hbm", "achieved": round(gbs_rw, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(gbs_rw / peak, 5), "traffic": traffic,
+                     "peak_source": f"{peak_src} copy bandwidth", "kernel": "k_solve<double>",
+                     "alg_bytes_per_launch": by_rw},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(us_e2e, 3), "unit": "us", "h2d_bytes_per_step": int(b.nbytes),
+                "d2h_bytes_per_step": int(b.nbytes)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,291 @@
+/*
+ * sptrsv.h -- C ABI of the GB300 (sm_103a) sparse lower-triangular solve library.
+ *
+ * Solves L x = b for a sparse lower-triangular L in CSR (arXiv 2206.05843, Section II.A)
+ * with the level-set method, either on L itself or after the paper's equation-rewriting
+ * graph transformation (Section II.B, Section III), which moves rows of thin levels up
+ * into earlier target levels so that the solve crosses fewer level barriers.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers; *_host are host pointers.  Matrix and
+ *     vector arguments are caller-owned; handles (levels, systems, batches, pickers)
+ *     are library-owned and freed by their *_destroy function.
+ *   - CSR: int32 row pointers (n+1) and column indices, columns strictly ascending in
+ *     each row, the diagonal stored as the LAST entry of the row and non-zero
+ *     (Algorithm 1 reads it at rowPtrL[i+1]-1).  Values float64 or float32.
+ *   - Right-hand sides and solutions are column-major n x nrhs with leading dimension
+ *     ld >= n; b and x must not overlap.
+ *   - Levels are numbered from 0.
+ *   - Calls are ordered on the given CUDA stream (NULL = the legacy default stream) and
+ *     asynchronous unless they return host data, in which case they synchronize the
+ *     stream before returning.
+ *   - No C++ exception crosses this boundary.  On failure a status code is returned and
+ *     sptrsv_last_error() holds a one-line message for the calling thread.
+ *   - Every device-side wait is bounded; a wait that runs out sets the status
+ *     SPTRSV_ERR_TIMEOUT and the kernel returns, leaving the CUDA context usable.
+ */
+#ifndef SPTRSV_H
+#define SPTRSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sptrsv_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    SPTRSV_OK = 0,
+    SPTRSV_ERR_INVALID = 1,     /* argument or CSR contract violated */
+    SPTRSV_ERR_OOM = 2,         /* device or host allocation failed */
+    SPTRSV_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    SPTRSV_ERR_TIMEOUT = 4,     /* a bounded device wait ran out */
+    SPTRSV_ERR_NUMERIC = 5,     /* rewrite growth guard tripped or non-finite value */
+    SPTRSV_ERR_UNSUPPORTED = 6  /* valid request outside what this build supports */
+} sptrsv_status;
+
+enum { SPTRSV_F64 = 0, SPTRSV_F32 = 1 };
+
+/* A lower-triangular CSR matrix in device memory (caller-owned). */
+typedef struct {
+    int64_t n;              /* rows = columns */
+    int64_t nnz;            /* entries, diagonal included; rowptr[n] == nnz */
+    const int32_t* rowptr;  /* device, n+1 */
+    const int32_t* colidx;  /* device, nnz */
+    const void* vals;       /* device, nnz values of type dtype */
+    int32_t dtype;          /* SPTRSV_F64 or SPTRSV_F32 */
+} sptrsv_csr;
+
+typedef struct sptrsv_levels sptrsv_levels;
+typedef struct sptrsv_system sptrsv_system;
+typedef struct sptrsv_batch sptrsv_batch;
+typedef struct sptrsv_picker sptrsv_picker;
+
+/* ---------------------------------------------------------------------------------
+ * Last error
+ * ------------------------------------------------------------------------------- */
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to len). */
+sptrsv_status sptrsv_last_error(char* buf_host, size_t len);
+
+/* ---------------------------------------------------------------------------------
+ * Validation and level-set analysis (Section II.A, Fig. 1)
+ * ------------------------------------------------------------------------------- */
+
+/* Checks the CSR contract on the device.  Returns SPTRSV_OK or SPTRSV_ERR_INVALID
+ * (message names the first offending row).  Synchronizes the stream. */
+sptrsv_status sptrsv_validate(const sptrsv_csr* L, sptrsv_stream_t stream);
+
+/* Level sets of DAG_L: a row without off-diagonal entries is on level 0, any other row
+ * one level below its deepest dependency (Section II.A).  Validates L first.  Computes
+ * level[n], the level pointer levelPtr[m+1], the rows of each level in ascending row
+ * order levelRows[n], and per-level rows / nnz / cost with cost = 2*sum(nnz) - rows
+ * (Section III).  *out is library-owned.  Synchronizes the stream (m is read back). */
+sptrsv_status sptrsv_analyse(const sptrsv_csr* L, sptrsv_levels** out, sptrsv_stream_t stream);
+
+typedef struct {
+    int64_t n;           /* rows */
+    int64_t m;           /* levels */
+    int64_t nnz;         /* entries of the analysed structure, diagonal included */
+    int64_t total_cost;  /* sum of level costs */
+    double avg_cost;     /* avgLevelCost = total_cost / m (Section III) */
+    int64_t max_width;   /* rows of the widest level */
+} sptrsv_level_stats;
+
+/* Host summary of an analysis.  No stream work. */
+sptrsv_status sptrsv_levels_stats(const sptrsv_levels* lv, sptrsv_level_stats* out_host);
+
+/* Copies the analysis to caller device buffers (any pointer may be NULL to skip):
+ * level[n], level_ptr[m+1], level_rows[n] (int32) and per-level rows / nnz / cost
+ * (int64, m each).  Stream-ordered. */
+sptrsv_status sptrsv_levels_export(const sptrsv_levels* lv, int32_t* level_dev, int32_t* level_ptr_dev,
+                                   int32_t* level_rows_dev, int64_t* rows_dev, int64_t* nnz_dev,
+                                   int64_t* cost_dev, sptrsv_stream_t stream);
+
+void sptrsv_levels_destroy(sptrsv_levels* lv);
+
+/* ---------------------------------------------------------------------------------
+ * Systems: what the solve runs on
+ * ------------------------------------------------------------------------------- */
+
+/* The plain level-set system of L: rows stored in level order, each normalised by its
+ * diagonal.  *out is library-owned.  Synchronizes the stream. */
+sptrsv_status sptrsv_system_plain(const sptrsv_csr* L, const sptrsv_levels* lv, sptrsv_system** out,
+                                  sptrsv_stream_t stream);
+
+enum {
+    SPTRSV_STRATEGY_NONE = 0,    /* no rewriting: same as sptrsv_system_plain */
+    SPTRSV_STRATEGY_NAIVE = 1,   /* Section III avgLevelCost strategy over thin levels */
+    SPTRSV_STRATEGY_DEPTH_K = 2, /* fixed distance: each target takes the next k levels (Section III, manual approach) */
+    SPTRSV_STRATEGY_LEARNED = 3, /* depth per target chosen by a trained picker (falls back to NAIVE without one) */
+    SPTRSV_STRATEGY_CHOSEN = 4   /* depth per target given by the caller */
+};
+
+typedef struct {
+    int32_t kind;                  /* SPTRSV_STRATEGY_* */
+    int32_t k;                     /* DEPTH_K: levels merged into each target */
+    double nnz_growth_cap;         /* > 0: nnz(L') + nnz(E) <= cap * nnz(L); <= 0: no cap */
+    double avg_override;           /* > 0: use this avgLevelCost instead of the computed one */
+    double growth_guard;           /* > 0: fail with SPTRSV_ERR_NUMERIC if a rewritten coefficient exceeds it in magnitude */
+    const sptrsv_picker* picker;   /* LEARNED */
+    const int32_t* depth_of_target_host; /* CHOSEN: depth for each level (m entries) when it is a target */
+    const int32_t* depths_host;    /* LEARNED: candidate depths (excluding 0); NULL = {1,2,4,8,16,32} */
+    int32_t n_depths;              /* entries of depths_host */
+    const int64_t* injected_cost_dev; /* test hook (NULL normally): per-row cost on the target used by
+                                         the planner instead of 2 * |dependencies after substitution| */
+} sptrsv_strategy;
+
+/* Plans the rewrite with the strategy, rewrites the chosen rows (substitution of every
+ * dependency on the target level or below it, then rearrangement into
+ * x_r + sum c_rk x_k = sum e_rm b_m; Section II.B, Fig. 2), re-levels the result, drops
+ * the emptied levels and stores it in level order.  *out is library-owned and solves
+ * the ORIGINAL system L x = b.  Synchronizes the stream. */
+sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels* lv, const sptrsv_strategy* strategy,
+                             sptrsv_system** out, sptrsv_stream_t stream);
+
+typedef struct {
+    int64_t n, m;          /* rows, levels of the stored system */
+    int64_t nnz_c;         /* stored off-diagonal coefficients (L' without its diagonal) */
+    int64_t nnz_e;         /* stored b-coefficients of rewritten rows, diagonal term excluded */
+    int64_t rows_moved;    /* rows rewritten to a higher level */
+    int64_t stored_nnz;    /* nnz(L') + nnz(E explicit rows) as the planner counts it */
+    int64_t nnz_l;         /* nnz(L) */
+    int64_t segments;      /* solve schedule: wide levels + single-CTA runs */
+    int64_t run_levels;    /* levels executed inside single-CTA runs */
+    int32_t dtype;
+    int32_t rewritten;
+    double avg_cost;       /* avgLevelCost used by the planner (0 for plain) */
+} sptrsv_system_info;
+
+sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);
+
+/* Exports the system in the ORIGINAL row numbering to caller device buffers sized from
+ * sptrsv_system_info_get (NULL skips an array):
+ *   target[n]   level each row was planned onto (original level numbering; int32)
+ *   level[n]    level of each row in the stored system (int32)
+ *   cptr[n+1], ccol[nnz_c], cval[nnz_c]  off-diagonal coefficients c_rk (x_r + sum c_rk x_k),
+ *               columns in original numbering, ascending within a row (int64 / int32 / dtype)
+ *   dinv[n]     1 / L_rr (dtype)
+ *   eptr[n+1], ecol[nnz_e], eval[nnz_e]  b-coefficients e_rm of rewritten rows, m != r (dtype)
+ * Stream-ordered. */
+sptrsv_status sptrsv_system_export(const sptrsv_system* s, int32_t* target_dev, int32_t* level_dev,
+                                   int64_t* cptr_dev, int32_t* ccol_dev, void* cval_dev, void* dinv_dev,
+                                   int64_t* eptr_dev, int32_t* ecol_dev, void* eval_dev, sptrsv_stream_t stream);
+
+void sptrsv_system_destroy(sptrsv_system* s);
+
+/* ---------------------------------------------------------------------------------
+ * Solve (Algorithm 1 executed level by level; Section II.A, Section V)
+ * ------------------------------------------------------------------------------- */
+
+/* x = L^{-1} b for nrhs right-hand sides (column-major, leading dimension ld >= n) in the
+ * system's value type.  One persistent kernel: wide levels are split over all CTAs and
+ * handed over through device-wide per-CTA completion flags; runs of thin levels execute
+ * inside one CTA.  Asynchronous; the status of the bounded waits is checked by the next
+ * host-returning call or by sptrsv_solve_status. */
+sptrsv_status sptrsv_solve(const sptrsv_system* s, const void* b_dev, void* x_dev, int32_t nrhs, int64_t ld,
+                           sptrsv_stream_t stream);
+
+/* Same as sptrsv_solve and, when stamps_dev is not NULL, records the %globaltimer
+ * nanosecond at which each stored level finished (uint64, m entries).  Used to harvest
+ * per-level times for the learned picker. */
+sptrsv_status sptrsv_solve_timed(const sptrsv_system* s, const void* b_dev, void* x_dev, int32_t nrhs, int64_t ld,
+                                 uint64_t* stamps_dev, sptrsv_stream_t stream);
+
+/* Synchronizes the stream and reports the device status word of the system's last
+ * solve (SPTRSV_OK or SPTRSV_ERR_TIMEOUT), then clears it. */
+sptrsv_status sptrsv_solve_status(const sptrsv_system* s, sptrsv_stream_t stream);
+
+/* Test hook for the bounded waits: the CTA that finishes schedule segment `segment`
+ * does not publish it, so every wait on it runs out after timeout_ns.  segment < 0
+ * disables the hook; timeout_ns <= 0 restores the default (2 s). */
+sptrsv_status sptrsv_debug_set_wait(sptrsv_system* s, int64_t withhold_segment, int64_t timeout_ns);
+
+/* Tuning knobs of one system (0 keeps the current value): block size of the persistent
+ * kernel, widest level executed inside a single-CTA run, lanes per row. */
+sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_width, int32_t lanes_per_row);
+
+/* ---------------------------------------------------------------------------------
+ * Batched solve
+ * ------------------------------------------------------------------------------- */
+
+/* Groups `count` systems (each solved for nrhs[i] right-hand sides, ld = n) into one
+ * persistent launch captured in a CUDA graph: every CTA takes whole matrices, longest
+ * critical path first, and crosses levels with CTA barriers.  Block size and lanes per
+ * row are autotuned by timing candidate launches; the choice is cached by the batch
+ * signature.  Systems must outlive the batch.  Synchronizes the stream. */
+sptrsv_status sptrsv_batch_create(const sptrsv_system* const* systems_host, const int32_t* nrhs_host, int32_t count,
+                                  sptrsv_batch** out, sptrsv_stream_t stream);
+
+/* Solves every system of the batch: b_host[i] / x_host[i] are DEVICE pointers held in a
+ * host array (column-major, ld = n_i).  Replays the captured graph. */
+sptrsv_status sptrsv_batch_solve(sptrsv_batch* bt, const void* const* b_host, void* const* x_host,
+                                 sptrsv_stream_t stream);
+
+typedef struct {
+    int32_t count, block, lanes_per_row, graph;
+    double tuned_us;       /* best measured time of the autotuner */
+} sptrsv_batch_info;
+
+sptrsv_status sptrsv_batch_info_get(const sptrsv_batch* bt, sptrsv_batch_info* out_host);
+
+void sptrsv_batch_destroy(sptrsv_batch* bt);
+
+/* ---------------------------------------------------------------------------------
+ * Learned rewrite picker: an MLP 12 -> 64 -> 64 -> 64 -> 1 (ReLU) with bfloat16 weights
+ * and float32 accumulation that predicts the solve-time change of rewriting the next
+ * g levels into a target level (the learned strategy the paper names as future work,
+ * Conclusion).
+ * ------------------------------------------------------------------------------- */
+
+#define SPTRSV_PICKER_FEATURES 12
+#define SPTRSV_PICKER_HIDDEN 64
+#define SPTRSV_PICKER_PARAMS (12 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* New picker with weights drawn from a seeded generator (Kaiming-uniform). */
+sptrsv_status sptrsv_picker_create(uint64_t seed, sptrsv_picker** out);
+void sptrsv_picker_destroy(sptrsv_picker* pk);
+
+/* Flat float32 parameter vector (SPTRSV_PICKER_PARAMS entries, layer by layer: W1 row-major
+ * [64][12], b1, W2 [64][64], b2, W3 [64][64], b3, W4 [1][64], b4) to or from the host. */
+sptrsv_status sptrsv_picker_get_params(const sptrsv_picker* pk, float* params_host);
+sptrsv_status sptrsv_picker_set_params(sptrsv_picker* pk, const float* params_host);
+
+/* Input normalisation applied before layer 1: f' = (f - mean) / std (12 each). */
+sptrsv_status sptrsv_picker_set_norm(sptrsv_picker* pk, const float* mean_host, const float* std_host,
+                                     float target_scale);
+
+/* Saves / loads weights, normalisation and optimiser state (binary with a text header). */
+sptrsv_status sptrsv_picker_save(const sptrsv_picker* pk, const char* path);
+sptrsv_status sptrsv_picker_load(sptrsv_picker* pk, const char* path);
+
+/* Features of every candidate (target level t, depth g) for t in [0, m) and g in depths:
+ * feat_dev[(t * n_depths + d) * 12 + f] (float32).  Stream-ordered. */
+sptrsv_status sptrsv_picker_features(const sptrsv_csr* L, const sptrsv_levels* lv, const int32_t* depths_host,
+                                     int32_t n_depths, float* feat_dev, sptrsv_stream_t stream);
+
+/* Predicted solve-time change (float32, in target units) for `count` feature rows.
+ * bf16_weights != 0 uses the bfloat16 copy of the weights, else the float32 master. */
+sptrsv_status sptrsv_picker_infer(const sptrsv_picker* pk, const float* feat_dev, int64_t count, float* out_dev,
+                                  int32_t bf16_weights, sptrsv_stream_t stream);
+
+/* Gradient of the mean squared error over `count` rows with respect to every parameter
+ * (float32, SPTRSV_PICKER_PARAMS entries) and the loss; forward through the bfloat16 or
+ * float32 weights.  Stream-ordered. */
+sptrsv_status sptrsv_picker_grad(const sptrsv_picker* pk, const float* feat_dev, const float* target_dev,
+                                 int64_t count, int32_t bf16_weights, float* grad_dev, float* loss_dev,
+                                 sptrsv_stream_t stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a mini-batch: gradient as above,
+ * then the float32 master weights, their bfloat16 copy and the moments are updated on
+ * the device.  loss_dev (may be NULL) receives the batch loss before the step. */
+sptrsv_status sptrsv_picker_train_step(sptrsv_picker* pk, const float* feat_dev, const float* target_dev,
+                                       int64_t count, float lr, float* loss_dev, sptrsv_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPTRSV_H */

@@ -1,0 +1,328 @@
+"""Thin Python binding of libsptrsv.so (the C ABI in include/sptrsv.h).
+
+Argument marshalling only: torch supplies device memory and the current CUDA stream,
+every step of analysis, rewriting and solving runs in the library's CUDA kernels.
+Importing this module does not touch the GPU; the first call loads the library and
+raises if it is missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsptrsv.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNSUPPORTED"}
+F64, F32 = 0, 1
+NONE, NAIVE, DEPTH_K, LEARNED, CHOSEN = 0, 1, 2, 3, 4
+PICKER_FEATURES, PICKER_HIDDEN = 12, 64
+PICKER_PARAMS = 12 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+
+# every symbol include/sptrsv.h declares
+EXPORTED = [
+    "sptrsv_last_error", "sptrsv_validate", "sptrsv_analyse", "sptrsv_levels_stats", "sptrsv_levels_export",
+    "sptrsv_levels_destroy", "sptrsv_system_plain", "sptrsv_rewrite", "sptrsv_system_info_get",
+    "sptrsv_system_export", "sptrsv_system_destroy", "sptrsv_solve", "sptrsv_solve_timed", "sptrsv_solve_status",
+    "sptrsv_debug_set_wait", "sptrsv_system_tune", "sptrsv_batch_create", "sptrsv_batch_solve",
+    "sptrsv_batch_info_get", "sptrsv_batch_destroy", "sptrsv_picker_create", "sptrsv_picker_destroy",
+    "sptrsv_picker_get_params", "sptrsv_picker_set_params", "sptrsv_picker_set_norm", "sptrsv_picker_save",
+    "sptrsv_picker_load", "sptrsv_picker_features", "sptrsv_picker_infer", "sptrsv_picker_grad",
+    "sptrsv_picker_train_step",
+]
+
+
+class SptrsvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colidx", C.c_void_p),
+                ("vals", C.c_void_p), ("dtype", C.c_int32)]
+
+
+class LevelStats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("nnz", C.c_int64), ("total_cost", C.c_int64),
+                ("avg_cost", C.c_double), ("max_width", C.c_int64)]
+
+
+class Strategy(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("k", C.c_int32), ("nnz_growth_cap", C.c_double),
+                ("avg_override", C.c_double), ("growth_guard", C.c_double), ("picker", C.c_void_p),
+                ("depth_of_target_host", C.c_void_p), ("depths_host", C.c_void_p), ("n_depths", C.c_int32),
+                ("injected_cost_dev", C.c_void_p)]
+
+
+class SystemInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("nnz_c", C.c_int64), ("nnz_e", C.c_int64),
+                ("rows_moved", C.c_int64), ("stored_nnz", C.c_int64), ("nnz_l", C.c_int64),
+                ("segments", C.c_int64), ("run_levels", C.c_int64), ("dtype", C.c_int32),
+                ("rewritten", C.c_int32), ("avg_cost", C.c_double)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("count", C.c_int32), ("block", C.c_int32), ("lanes_per_row", C.c_int32), ("graph", C.c_int32),
+                ("tuned_us", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Loads libsptrsv.so; raises when it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2206_05843_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "sptrsv_last_error": [C.c_char_p, C.c_size_t],
+            "sptrsv_validate": [vp, vp],
+            "sptrsv_analyse": [vp, C.POINTER(vp), vp],
+            "sptrsv_levels_stats": [vp, vp],
+            "sptrsv_levels_export": [vp, vp, vp, vp, vp, vp, vp, vp],
+            "sptrsv_system_plain": [vp, vp, C.POINTER(vp), vp],
+            "sptrsv_rewrite": [vp, vp, vp, C.POINTER(vp), vp],
+            "sptrsv_system_info_get": [vp, vp],
+            "sptrsv_system_export": [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "sptrsv_solve": [vp, vp, vp, i32, i64, vp],
+            "sptrsv_solve_timed": [vp, vp, vp, i32, i64, vp, vp],
+            "sptrsv_solve_status": [vp, vp],
+            "sptrsv_debug_set_wait": [vp, i64, i64],
+            "sptrsv_system_tune": [vp, i32, i32, i32],
+            "sptrsv_batch_create": [vp, vp, i32, C.POINTER(vp), vp],
+            "sptrsv_batch_solve": [vp, vp, vp, vp],
+            "sptrsv_batch_info_get": [vp, vp],
+            "sptrsv_picker_create": [C.c_uint64, C.POINTER(vp)],
+            "sptrsv_picker_get_params": [vp, vp],
+            "sptrsv_picker_set_params": [vp, vp],
+            "sptrsv_picker_set_norm": [vp, vp, vp, C.c_float],
+            "sptrsv_picker_save": [vp, C.c_char_p],
+            "sptrsv_picker_load": [vp, C.c_char_p],
+            "sptrsv_picker_features": [vp, vp, vp, i32, vp, vp],
+            "sptrsv_picker_infer": [vp, vp, i64, vp, i32, vp],
+            "sptrsv_picker_grad": [vp, vp, vp, i64, i32, vp, vp, vp],
+            "sptrsv_picker_train_step": [vp, vp, vp, i64, C.c_float, vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        for name in ("sptrsv_levels_destroy", "sptrsv_system_destroy", "sptrsv_batch_destroy",
+                     "sptrsv_picker_destroy"):
+            f = getattr(lib, name)
+            f.argtypes = [vp]
+            f.restype = None
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    load().sptrsv_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(code: int):
+    if code != OK:
+        raise SptrsvError(code, last_error())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+# ------------------------------------------------------------------------------------
+# matrices
+# ------------------------------------------------------------------------------------
+
+class Matrix:
+    """A lower-triangular CSR matrix resident on the GPU (tensors kept alive here)."""
+
+    def __init__(self, n, rowptr, colidx, vals):
+        torch = _torch()
+        self.n = int(n)
+        self.rowptr = rowptr
+        self.colidx = colidx
+        self.vals = vals
+        self.dtype = F64 if vals.dtype == torch.float64 else F32
+        self.csr = Csr(self.n, int(colidx.numel()), rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr(), self.dtype)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    @classmethod
+    def from_host(cls, m, device="cuda", dtype=None):
+        """From a synth.LowerCsr (or anything with n/rowptr/colidx/vals numpy arrays)."""
+        torch = _torch()
+        vals = np.asarray(m.vals)
+        if dtype is not None:
+            vals = vals.astype(dtype)
+        tdt = torch.float64 if vals.dtype == np.float64 else torch.float32
+        rp = torch.from_numpy(np.ascontiguousarray(m.rowptr, dtype=np.int32)).to(device)
+        ci = torch.from_numpy(np.ascontiguousarray(m.colidx, dtype=np.int32)).to(device)
+        va = torch.from_numpy(np.ascontiguousarray(vals)).to(device=device, dtype=tdt)
+        return cls(m.n, rp, ci, va)
+
+    def validate(self):
+        check(load().sptrsv_validate(C.byref(self.csr), _stream()))
+
+
+class Levels:
+    def __init__(self, matrix: Matrix):
+        h = C.c_void_p()
+        check(load().sptrsv_analyse(C.byref(matrix.csr), C.byref(h), _stream()))
+        self.h = h
+        self.matrix = matrix
+        st = LevelStats()
+        check(load().sptrsv_levels_stats(h, C.byref(st)))
+        self.n, self.m, self.nnz = st.n, st.m, st.nnz
+        self.total_cost, self.avg_cost, self.max_width = st.total_cost, st.avg_cost, st.max_width
+
+    def export(self) -> dict:
+        torch = _torch()
+        dev = self.matrix.rowptr.device
+        n, m = self.n, self.m
+        level = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        lptr = torch.empty(m + 1, dtype=torch.int32, device=dev)
+        lrows = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        rows = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+        nnz = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+        cost = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+        check(load().sptrsv_levels_export(self.h, _ptr(level), _ptr(lptr), _ptr(lrows), _ptr(rows), _ptr(nnz),
+                                          _ptr(cost), _stream()))
+        return {"level": level[:n].cpu().numpy(), "level_ptr": lptr.cpu().numpy(), "level_rows": lrows[:n].cpu().numpy(),
+                "rows": rows[:m].cpu().numpy(), "nnz": nnz[:m].cpu().numpy(), "cost": cost[:m].cpu().numpy()}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sptrsv_levels_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def strategy(kind=NONE, k=0, cap=0.0, avg=0.0, guard=0.0, picker=None, depth_of_target=None, depths=None,
+             injected_cost=None) -> tuple[Strategy, list]:
+    """Builds an sptrsv_strategy; returns it with the objects that must stay alive."""
+    keep = []
+    s = Strategy()
+    s.kind, s.k, s.nnz_growth_cap, s.avg_override, s.growth_guard = kind, k, cap, avg, guard
+    s.picker = picker.h if picker is not None else None
+    if depth_of_target is not None:
+        a = np.ascontiguousarray(depth_of_target, dtype=np.int32)
+        keep.append(a)
+        s.depth_of_target_host = a.ctypes.data
+    if depths is not None:
+        a = np.ascontiguousarray(depths, dtype=np.int32)
+        keep.append(a)
+        s.depths_host = a.ctypes.data
+        s.n_depths = a.size
+    if injected_cost is not None:
+        keep.append(injected_cost)
+        s.injected_cost_dev = injected_cost.data_ptr()
+    return s, keep
+
+
+class System:
+    """A stored system (plain or rewritten) that sptrsv_solve runs on."""
+
+    def __init__(self, matrix: Matrix, levels: Levels, kind=NONE, **kw):
+        h = C.c_void_p()
+        if kind == NONE and not kw:
+            check(load().sptrsv_system_plain(C.byref(matrix.csr), levels.h, C.byref(h), _stream()))
+        else:
+            s, keep = strategy(kind, **kw)
+            check(load().sptrsv_rewrite(C.byref(matrix.csr), levels.h, C.byref(s), C.byref(h), _stream()))
+            del keep
+        self.h = h
+        self.matrix = matrix
+        self.dtype = matrix.dtype
+        self.refresh()
+
+    def refresh(self):
+        inf = SystemInfo()
+        check(load().sptrsv_system_info_get(self.h, C.byref(inf)))
+        self.info = {f: getattr(inf, f) for f, _ in SystemInfo._fields_}
+        self.n, self.m = inf.n, inf.m
+        return self.info
+
+    def tune(self, block=0, run_width=0, lanes_per_row=0):
+        check(load().sptrsv_system_tune(self.h, block, run_width, lanes_per_row))
+
+    def debug_set_wait(self, withhold_segment=-1, timeout_ns=0):
+        check(load().sptrsv_debug_set_wait(self.h, withhold_segment, timeout_ns))
+
+    def solve(self, b, x=None, stamps=None, check_status=False):
+        """b: device tensor of shape (n,) or (nrhs, n) (column-major n x nrhs, ld = n)."""
+        torch = _torch()
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        if x is None:
+            x = torch.empty_like(b)
+        if stamps is None:
+            check(load().sptrsv_solve(self.h, _ptr(b), _ptr(x), nrhs, self.n, _stream()))
+        else:
+            check(load().sptrsv_solve_timed(self.h, _ptr(b), _ptr(x), nrhs, self.n, _ptr(stamps), _stream()))
+        if check_status:
+            self.status()
+        return x
+
+    def status(self):
+        check(load().sptrsv_solve_status(self.h, _stream()))
+
+    def export(self) -> dict:
+        torch = _torch()
+        self.refresh()
+        dev = self.matrix.rowptr.device
+        n, nc, ne = self.n, self.info["nnz_c"], self.info["nnz_e"]
+        vt = torch.float64 if self.dtype == F64 else torch.float32
+        target = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        level = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        cptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        ccol = torch.empty(max(nc, 1), dtype=torch.int32, device=dev)
+        cval = torch.empty(max(nc, 1), dtype=vt, device=dev)
+        dinv = torch.empty(max(n, 1), dtype=vt, device=dev)
+        eptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        ecol = torch.empty(max(ne, 1), dtype=torch.int32, device=dev)
+        evl = torch.empty(max(ne, 1), dtype=vt, device=dev)
+        check(load().sptrsv_system_export(self.h, _ptr(target), _ptr(level), _ptr(cptr), _ptr(ccol), _ptr(cval),
+                                          _ptr(dinv), _ptr(eptr), _ptr(ecol), _ptr(evl), _stream()))
+        out = {"target": target[:n], "level": level[:n], "cptr": cptr, "ccol": ccol[:nc], "cval": cval[:nc],
+               "dinv": dinv[:n], "eptr": eptr, "ecol": ecol[:ne], "eval": evl[:ne]}
+        return {k: v.cpu().numpy() for k, v in out.items()}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sptrsv_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

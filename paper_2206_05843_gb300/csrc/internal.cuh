@@ -1,0 +1,169 @@
+// internal.cuh -- shared declarations of the sm_103a SpTRSV library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sptrsv.h"
+
+namespace sp {
+
+// ---------------------------------------------------------------------------------
+// error plumbing: every ABI entry point returns a status; the message is per thread
+// ---------------------------------------------------------------------------------
+
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+#define SP_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::sp::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? SPTRSV_ERR_OOM : SPTRSV_ERR_CUDA;  \
+        }                                                                               \
+    } while (0)
+
+#define SP_TRY(expr)                              \
+    do {                                          \
+        sptrsv_status s_ = (expr);                \
+        if (s_ != SPTRSV_OK) return s_;           \
+    } while (0)
+
+// device buffer owned by a handle; freed with cudaFree on destruction
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    // allocates count elements plus 64 bytes of tail padding (bulk copies may round the
+    // end of a range up to 16 bytes)
+    sptrsv_status alloc(size_t count) {
+        release();
+        size_t bytes = count * sizeof(T) + 64;
+        cudaError_t e = cudaMalloc((void**)&p, bytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? SPTRSV_ERR_OOM : SPTRSV_ERR_CUDA;
+        }
+        n = count;
+        return SPTRSV_OK;
+    }
+    sptrsv_status ensure(size_t count) { return count <= n && p ? SPTRSV_OK : alloc(count); }
+    T* get() const { return p; }
+};
+
+// stream-ordered scratch (cudaMallocAsync) freed when the object goes out of scope
+struct Scratch {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    Scratch() = default;
+    Scratch(const Scratch&) = delete;
+    ~Scratch() {
+        if (p) cudaFreeAsync(p, st);
+    }
+    sptrsv_status alloc(size_t bytes, cudaStream_t s) {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        st = s;
+        cudaError_t e = cudaMallocAsync(&p, bytes + 64, s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? SPTRSV_ERR_OOM : SPTRSV_ERR_CUDA;
+        }
+        return SPTRSV_OK;
+    }
+    template <typename T>
+    T* as() const { return (T*)p; }
+};
+
+int device_sm_count();
+int64_t default_timeout_ns();
+
+// ---------------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------------
+
+#ifdef __CUDACC__
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int* p) {
+    int v;
+    asm volatile("ld.volatile.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#endif
+
+// status words written by kernels (device int, 0 = ok)
+enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NUMERIC = 2, DEV_OVERFLOW = 3, DEV_INVALID = 4 };
+
+sptrsv_status map_dev_status(int code, const char* where);
+
+// ---------------------------------------------------------------------------------
+// primitives (prims.cu)
+// ---------------------------------------------------------------------------------
+
+// exclusive scan of n values into out[0..n]; out[n] = total.  in and out may alias.
+sptrsv_status scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+sptrsv_status scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+// scan of int32 counts into int64 offsets
+sptrsv_status scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st);
+
+// stable sort of (key, value) pairs by key (keys in [0, 2^bits)); results in keys_out/vals_out
+sptrsv_status radix_sort_pairs(const int32_t* keys_in, const int32_t* vals_in, int32_t* keys_out,
+                               int32_t* vals_out, int64_t n, int bits, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------
+// analysis (analyse.cu)
+// ---------------------------------------------------------------------------------
+
+// a dependency structure: row i depends on colidx[rowptr[i] .. rowptr[i+1] - diag_last)
+struct DepCsr {
+    int64_t n = 0;
+    const int32_t* rowptr = nullptr;
+    const int32_t* colidx = nullptr;
+    int diag_last = 1;
+};
+
+struct Levels {
+    int64_t n = 0, m = 0, nnz = 0, total_cost = 0, max_width = 0;
+    double avg = 0.0;
+    DevBuf<int32_t> level, level_ptr, level_rows, pos;
+    DevBuf<int64_t> lrows, lnnz, lcost;
+    std::vector<int32_t> h_level_ptr;
+    std::vector<int64_t> h_lcost;
+};
+
+sptrsv_status validate_csr(const sptrsv_csr* L, cudaStream_t st);
+sptrsv_status analyse_dep(const DepCsr& d, Levels& out, cudaStream_t st);
+
+}  // namespace sp
+
+// opaque handle types of the ABI
+struct sptrsv_levels {
+    sp::Levels lv;
+};

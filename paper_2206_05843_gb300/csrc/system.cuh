@@ -1,0 +1,109 @@
+// system.cuh -- the stored system and the solve schedule (internal).
+#pragma once
+
+#include "internal.cuh"
+
+namespace sp {
+
+enum SegType : int { SEG_WIDE = 0, SEG_RUN = 1 };
+
+// A segment of the persistent solve.  WIDE: one level split over CTAs 0..parts-1.
+// RUN: consecutive thin levels executed by CTA 0 alone, staged block by block.
+// int4 layout: {type, a, b, c}
+//   WIDE: a = level, b = rows per participating CTA, c = number of participating CTAs
+//   RUN : a = first block, b = end block, c = 0
+// A run block: int4 {first level, end level, narrow (all levels fit one warp), 0}
+
+struct Schedule {
+    int nrhs = -1, block = 0, run_width = 0, lpr = 0, grid = 0, ring_rows = 0;
+    int stage_rows = 0, stage_entries = 0;
+    size_t smem = 0;
+    int64_t run_levels = 0;
+    std::vector<int4> h_segs, h_blocks;
+    DevBuf<int4> segs, blocks;
+};
+
+// rows in the stored order ("positions"): perm[p] = original row; ccol holds positions
+template <typename T>
+struct SolveArgs {
+    int64_t n;
+    int nrhs;
+    int64_t ld;
+    const int32_t* __restrict__ perm;
+    const int32_t* __restrict__ lptr;
+    const int32_t* __restrict__ cptr;
+    const int32_t* __restrict__ ccol;
+    const T* __restrict__ cval;
+    const T* __restrict__ dinv;
+    const int32_t* __restrict__ eptr;  // nullptr when no row was rewritten
+    const int32_t* __restrict__ ecol;
+    const T* __restrict__ eval;
+    const int4* __restrict__ segs;
+    const int4* __restrict__ blocks;
+    int nseg;
+    const T* __restrict__ b;
+    T* x;
+    T* xp;  // solution in stored order, position-major: xp[p * nrhs + k]
+    int* flags;
+    int* status;
+    unsigned long long* stamps;
+    int withhold;
+    int64_t timeout_ns;
+    int ring_rows;  // power of two
+    int lpr;        // lanes per row (power of two <= 32)
+    int stage_rows, stage_entries;
+};
+
+}  // namespace sp
+
+struct sptrsv_system {
+    int64_t n = 0, m = 0;
+    int dtype = SPTRSV_F64;
+    int rewritten = 0;
+    sp::Levels lv;  // levels of the stored structure; lv.level_rows is perm, lv.pos its inverse
+    sp::DevBuf<int32_t> cptr, ccol, eptr, ecol, target;
+    sp::DevBuf<unsigned char> cval, eval, dinv;
+    int64_t nnz_c = 0, nnz_e = 0, rows_moved = 0, stored_nnz = 0, nnz_l = 0;
+    double avg = 0.0;
+    // solve state
+    int block = 512, run_width = 0, lpr = 0;  // 0: automatic
+    sp::Schedule sched;
+    sp::DevBuf<int> flags, status;
+    sp::DevBuf<unsigned char> xp;
+    int withhold = -1;
+    int64_t timeout_ns = 0;
+};
+
+namespace sp {
+
+// builds (or reuses) the schedule of a system for nrhs right-hand sides
+sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs);
+
+// enqueues one solve (flags/status reset + persistent kernel) on the stream
+sptrsv_status enqueue_solve(sptrsv_system* s, const void* b, void* x, int nrhs, int64_t ld,
+                            unsigned long long* stamps, cudaStream_t st);
+
+// fills the stored arrays of a system from L (rows that were not rewritten) and, when
+// moved != nullptr, from the rewrite heap (rows with moved[r] != 0).  s->lv must hold
+// the levels of the final structure.
+struct RewriteHeap {
+    const int32_t* moved = nullptr;
+    const int64_t* c_off = nullptr;
+    const int32_t* c_cnt = nullptr;
+    const int64_t* e_off = nullptr;
+    const int32_t* e_cnt = nullptr;
+    const int32_t* col = nullptr;
+    const double* val = nullptr;
+};
+sptrsv_status pack_system(sptrsv_system* s, const sptrsv_csr* L, const RewriteHeap* rw, cudaStream_t st);
+
+// rewrite with a planner walk kind (1 naive, 2 fixed depth, 3 depth per target) -> new system
+sptrsv_status rewrite_system(const sptrsv_csr* L, const Levels& lv, int kind, int k, const int32_t* dot_dev,
+                             double avg_override, double cap, double guard, const int64_t* inj, sptrsv_system** out,
+                             cudaStream_t st);
+
+// the learned strategy (picker.cu): features -> MLP -> depth per target -> rewrite_system
+sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lv, const sptrsv_strategy* sg,
+                              sptrsv_system** out, cudaStream_t st);
+
+}  // namespace sp

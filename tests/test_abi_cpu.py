@@ -1,0 +1,41 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads without a GPU and
+exports every entry point that include/sptrsv.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+from paper_2206_05843_gb300 import binding
+from paper_2206_05843_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "sptrsv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(sptrsv_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build()
+    lib = ctypes.CDLL(path)
+    names = declared_symbols()
+    assert len(names) >= 25
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(names) == sorted(binding.EXPORTED)
+
+
+def test_binding_loads_signatures():
+    lib = binding.load()
+    for n in binding.EXPORTED:
+        assert getattr(lib, n).restype is not None or n.endswith("destroy")
+
+
+def test_strategy_struct_layout_matches_header():
+    # the binding mirrors the header's struct field order
+    src = open(os.path.join(ROOT, "include", "sptrsv.h")).read()
+    body = src[src.index("typedef struct {\n    int32_t kind;"):src.index("} sptrsv_strategy;")]
+    fields = re.findall(r"\*?\s*([a-z_0-9]+);", body)
+    assert fields == [f for f, _ in binding.Strategy._fields_]
