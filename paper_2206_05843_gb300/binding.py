@@ -326,3 +326,124 @@ class System:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many systems solved in one graph-captured persistent launch."""
+
+    def __init__(self, systems, nrhs):
+        nrhs = [int(r) for r in nrhs]
+        assert len(systems) == len(nrhs) and systems
+        self.systems = list(systems)
+        self.nrhs = nrhs
+        arr = (C.c_void_p * len(systems))(*[s.h.value if isinstance(s.h, C.c_void_p) else s.h for s in systems])
+        nr = (C.c_int32 * len(systems))(*nrhs)
+        h = C.c_void_p()
+        check(load().sptrsv_batch_create(arr, nr, len(systems), C.byref(h), _stream()))
+        self.h = h
+        inf = BatchInfo()
+        check(load().sptrsv_batch_info_get(h, C.byref(inf)))
+        self.info = {f: getattr(inf, f) for f, _ in BatchInfo._fields_}
+
+    def solve(self, bs, xs=None):
+        """bs: list of device tensors (nrhs_i, n_i) in each system's value type."""
+        torch = _torch()
+        if xs is None:
+            xs = [torch.empty_like(b) for b in bs]
+        n = len(self.systems)
+        barr = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+        xarr = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        check(load().sptrsv_batch_solve(self.h, barr, xarr, _stream()))
+        return xs
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sptrsv_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Picker:
+    """The learned rewrite picker (MLP 12 -> 64 -> 64 -> 64 -> 1, bfloat16 weights)."""
+
+    def __init__(self, seed: int = 0):
+        h = C.c_void_p()
+        check(load().sptrsv_picker_create(C.c_uint64(seed), C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def load(cls, path: str) -> "Picker":
+        pk = cls(0)
+        check(load().sptrsv_picker_load(pk.h, path.encode()))
+        return pk
+
+    def save(self, path: str):
+        check(load().sptrsv_picker_save(self.h, path.encode()))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(PICKER_PARAMS, dtype=np.float32)
+        check(load().sptrsv_picker_get_params(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        assert a.size == PICKER_PARAMS
+        check(load().sptrsv_picker_set_params(self.h, a.ctypes.data_as(C.c_void_p)))
+
+    def set_norm(self, mean, std, target_scale=1.0):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        s = np.ascontiguousarray(std, dtype=np.float32)
+        check(load().sptrsv_picker_set_norm(self.h, m.ctypes.data_as(C.c_void_p), s.ctypes.data_as(C.c_void_p),
+                                            C.c_float(target_scale)))
+
+    def infer(self, feat, bf16=True):
+        torch = _torch()
+        n = feat.shape[0]
+        out = torch.empty(max(n, 1), dtype=torch.float32, device=feat.device)
+        check(load().sptrsv_picker_infer(self.h, _ptr(feat), n, _ptr(out), 1 if bf16 else 0, _stream()))
+        return out[:n]
+
+    def grad(self, feat, target, bf16=True):
+        torch = _torch()
+        g = torch.empty(PICKER_PARAMS, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        check(load().sptrsv_picker_grad(self.h, _ptr(feat), _ptr(target), feat.shape[0], 1 if bf16 else 0, _ptr(g),
+                                        _ptr(loss), _stream()))
+        return g, loss
+
+    def train_step(self, feat, target, lr):
+        torch = _torch()
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        check(load().sptrsv_picker_train_step(self.h, _ptr(feat), _ptr(target), feat.shape[0], C.c_float(lr),
+                                              _ptr(loss), _stream()))
+        return loss
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sptrsv_picker_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+DEFAULT_DEPTHS = (1, 2, 4, 8, 16, 32)
+
+
+def features(matrix: Matrix, levels: Levels, depths=DEFAULT_DEPTHS):
+    """Device tensor (m * len(depths), 12) of candidate features, row t * len(depths) + d."""
+    torch = _torch()
+    d = np.ascontiguousarray(depths, dtype=np.int32)
+    out = torch.empty((max(levels.m * d.size, 1), PICKER_FEATURES), dtype=torch.float32,
+                      device=matrix.rowptr.device)
+    check(load().sptrsv_picker_features(C.byref(matrix.csr), levels.h, d.ctypes.data_as(C.c_void_p), d.size,
+                                        _ptr(out), _stream()))
+    return out[:levels.m * d.size]

@@ -10,47 +10,12 @@
 // separated by a CTA (or warp) barrier instead of a device-wide handoff.
 #include <algorithm>
 
-#include "system.cuh"
+#include "run_exec.cuh"
 
 namespace sp {
 namespace {
 
-struct Lanes {
-    int lpr, RL, EL, rl, el, chunks;
-};
-
-__device__ __forceinline__ Lanes make_lanes(int lpr, int nrhs) {
-    Lanes l;
-    l.lpr = lpr;
-    int p2 = 1;
-    while (p2 < nrhs && p2 < lpr) p2 <<= 1;
-    l.RL = p2;
-    l.EL = lpr / p2;
-    int lg = threadIdx.x & (lpr - 1);
-    l.rl = lg % l.RL;
-    l.el = lg / l.RL;
-    l.chunks = (nrhs + l.RL - 1) / l.RL;
-    return l;
-}
-
-template <typename T>
-__device__ __forceinline__ T group_reduce(T v, const Lanes& ln) {
-    for (int o = ln.RL; o < ln.lpr; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// b-part of row p for right-hand side k, partial over this lane's share of the E row
-template <typename T>
-__device__ __forceinline__ T bpart(const SolveArgs<T>& a, int64_t p, int32_t row, int k, const Lanes& ln) {
-    T acc = T(0);
-    if (ln.el == 0) acc = a.dinv[p] * a.b[(int64_t)row + (int64_t)k * a.ld];
-    if (a.eptr) {
-        int e1 = a.eptr[p + 1];
-        for (int q = a.eptr[p] + ln.el; q < e1; q += ln.EL)
-            acc += a.eval[q] * a.b[(int64_t)a.ecol[q] + (int64_t)k * a.ld];
-    }
-    return acc;
-}
+constexpr int PF = 6;  // coefficients of a wide-level row prefetched into registers before the wait
 
 // ---------------------------------------------------------------------------------
 // bounded waits and publication
@@ -89,26 +54,31 @@ __device__ __forceinline__ void publish(const SolveArgs<T>& a, int s) {
     }
 }
 
+// b-part partial over this lane's share of the E row (lanes split the row)
+template <typename T>
+__device__ __forceinline__ T bpart(const SolveArgs<T>& a, int64_t p, int32_t row, int k, const Lanes& ln) {
+    T acc = T(0);
+    if (ln.el == 0) acc = a.dinv[p] * a.b[(int64_t)row + (int64_t)k * a.ld];
+    if (a.eptr) {
+        int e1 = a.eptr[p + 1];
+        for (int q = a.eptr[p] + ln.el; q < e1; q += ln.EL)
+            acc += a.eval[q] * a.b[(int64_t)a.ecol[q] + (int64_t)k * a.ld];
+    }
+    return acc;
+}
+
 // ---------------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_solve(SolveArgs<T> a) {
+__global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int nrhs = a.nrhs;
-    T* ring = (T*)smem;
-    T* s_bp = ring + (size_t)a.ring_rows * nrhs;
-    T* s_cval = s_bp + (size_t)a.stage_rows * nrhs;
-    int32_t* s_ccol = (int32_t*)(s_cval + a.stage_entries);
-    int32_t* s_cptr = s_ccol + a.stage_entries;
-    int32_t* s_row = s_cptr + a.stage_rows + 1;
-
     const Lanes ln = make_lanes(a.lpr, nrhs);
     const int ngroups = blockDim.x / a.lpr;
     const int grp = threadIdx.x / a.lpr;
-    const int G = gridDim.x, me = blockIdx.x;
-    const int ring_mask = a.ring_rows - 1;
+    const int me = blockIdx.x;
 
     for (int s = 0; s < a.nseg; ++s) {
         const int4 sg = a.segs[s];
@@ -118,26 +88,49 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs<T> a) {
             const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
             const int64_t my0 = p0 + (int64_t)me * sg.z;
             const int64_t my1 = min(p1, my0 + (int64_t)sg.z);
-            // independent part of the first row before the wait: b-part (dinv b + E b)
+            // everything of the first row that does not depend on x, before the wait
             const int64_t pf = my0 + grp;
             const bool act0 = pf < my1;
+            const bool single = ln.chunks == 1;
             const int32_t row0 = act0 ? a.perm[pf] : 0;
+            const int f0 = act0 ? a.cptr[pf] : 0, f1 = act0 ? a.cptr[pf + 1] : 0;
             T pre = T(0);
-            if (act0 && ln.chunks == 1 && ln.rl < nrhs) pre = bpart(a, pf, row0, ln.rl, ln);
+            int32_t pcol[PF];
+            T pval[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int q = f0 + ln.el + u * ln.EL;
+                const bool ok = single && q < f1;
+                pcol[u] = ok ? a.ccol[q] : -1;
+                pval[u] = ok ? a.cval[q] : T(0);
+            }
+            if (act0 && single && ln.rl < nrhs) pre = bpart(a, pf, row0, ln.rl, ln);
             if (!wait_segment(a, s - 1)) return;
-            for (int64_t base = my0; base < my1; base += ngroups) {
+            int64_t base = my0;
+            const bool two = nrhs == 1 && a.lpr == 1;
+            for (; base < my1; base += ngroups) {
                 const int64_t p = base + grp;
                 const bool act = p < my1;
-                const int32_t row = act ? (base == my0 ? row0 : a.perm[p]) : 0;
-                const int c0 = act ? a.cptr[p] : 0, c1 = act ? a.cptr[p + 1] : 0;
+                const bool first = base == my0;
+                if (!first && two) break;  // the rest goes two rows per thread below
+                const int32_t row = act ? (first ? row0 : a.perm[p]) : 0;
+                const int c0 = act ? (first ? f0 : a.cptr[p]) : 0, c1 = act ? (first ? f1 : a.cptr[p + 1]) : 0;
                 for (int j = 0; j < ln.chunks; ++j) {
                     const int k = ln.rl + j * ln.RL;
                     const bool kv = act && k < nrhs;
                     T acc = T(0);
                     if (kv) {
-                        acc = (base == my0 && ln.chunks == 1) ? pre : bpart(a, p, row, k, ln);
-                        for (int q = c0 + ln.el; q < c1; q += ln.EL)
-                            acc -= a.cval[q] * __ldcg(a.xp + (int64_t)a.ccol[q] * nrhs + k);
+                        int q = c0 + ln.el;
+                        if (first && single) {
+                            acc = pre;
+#pragma unroll
+                            for (int u = 0; u < PF; ++u)
+                                if (pcol[u] >= 0) acc -= pval[u] * __ldcg(a.xp + (int64_t)pcol[u] * nrhs + k);
+                            q += PF * ln.EL;
+                        } else {
+                            acc = bpart(a, p, row, k, ln);
+                        }
+                        for (; q < c1; q += ln.EL) acc -= a.cval[q] * __ldcg(a.xp + (int64_t)a.ccol[q] * nrhs + k);
                     }
                     acc = group_reduce(acc, ln);
                     if (kv && ln.el == 0) {
@@ -146,90 +139,58 @@ __global__ void __launch_bounds__(1024) k_solve(SolveArgs<T> a) {
                     }
                 }
             }
+            // one right-hand side, a row per thread: two independent rows in flight
+            for (; base < my1; base += 2 * ngroups) {
+                const int64_t pa = base + grp, pb = pa + ngroups;
+                const bool aa = pa < my1, ab = pb < my1;
+                const int32_t ra = aa ? a.perm[pa] : 0, rb = ab ? a.perm[pb] : 0;
+                const int ca0 = aa ? a.cptr[pa] : 0, ca1 = aa ? a.cptr[pa + 1] : 0;
+                const int cb0 = ab ? a.cptr[pb] : 0, cb1 = ab ? a.cptr[pb + 1] : 0;
+                T acc_a = aa ? a.dinv[pa] * a.b[ra] : T(0);
+                T acc_b = ab ? a.dinv[pb] * a.b[rb] : T(0);
+                if (a.eptr) {
+                    const int ea0 = aa ? a.eptr[pa] : 0, ea1 = aa ? a.eptr[pa + 1] : 0;
+                    const int eb0 = ab ? a.eptr[pb] : 0, eb1 = ab ? a.eptr[pb + 1] : 0;
+                    for (int q = ea0; q < ea1; ++q) acc_a += a.eval[q] * a.b[a.ecol[q]];
+                    for (int q = eb0; q < eb1; ++q) acc_b += a.eval[q] * a.b[a.ecol[q]];
+                }
+                const int la = ca1 - ca0, lb = cb1 - cb0;
+                const int lmax = la > lb ? la : lb;
+                for (int u = 0; u < lmax; ++u) {
+                    T xa = T(0), xb = T(0), va = T(0), vb = T(0);
+                    if (u < la) {
+                        va = a.cval[ca0 + u];
+                        xa = __ldcg(a.xp + a.ccol[ca0 + u]);
+                    }
+                    if (u < lb) {
+                        vb = a.cval[cb0 + u];
+                        xb = __ldcg(a.xp + a.ccol[cb0 + u]);
+                    }
+                    if (u < la) acc_a -= va * xa;
+                    if (u < lb) acc_b -= vb * xb;
+                }
+                if (aa) {
+                    __stcg(a.xp + pa, acc_a);
+                    a.x[ra] = acc_a;
+                }
+                if (ab) {
+                    __stcg(a.xp + pb, acc_b);
+                    a.x[rb] = acc_b;
+                }
+            }
             publish(a, s);
             if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
         } else {
             if (me != 0) continue;
-            const int blk0 = sg.y, blk1 = sg.z;
-            const int64_t run_p0 = a.lptr[a.blocks[blk0].x];
-            bool waited = false;
-            for (int blk = blk0; blk < blk1; ++blk) {
-                const int4 bd = a.blocks[blk];
-                const int64_t P0 = a.lptr[bd.x], P1 = a.lptr[bd.y];
-                const int64_t Q0 = a.cptr[P0], Q1 = a.cptr[P1];
-                const int rows = (int)(P1 - P0), ents = (int)(Q1 - Q0);
-                __syncthreads();  // the previous block is done with the staging area
-                for (int i = threadIdx.x; i <= rows; i += blockDim.x) {
-                    s_cptr[i] = (int32_t)(a.cptr[P0 + i] - Q0);
-                    if (i < rows) s_row[i] = a.perm[P0 + i];
-                }
-                for (int j = threadIdx.x; j < ents; j += blockDim.x) {
-                    s_ccol[j] = a.ccol[Q0 + j];
-                    s_cval[j] = a.cval[Q0 + j];
-                }
-                for (int base = 0; base < rows; base += ngroups) {
-                    const int i = base + grp;
-                    const bool act = i < rows;
-                    const int32_t row = act ? a.perm[P0 + i] : 0;
-                    for (int j = 0; j < ln.chunks; ++j) {
-                        const int k = ln.rl + j * ln.RL;
-                        const bool kv = act && k < nrhs;
-                        T acc = kv ? bpart(a, P0 + i, row, k, ln) : T(0);
-                        acc = group_reduce(acc, ln);
-                        if (kv && ln.el == 0) s_bp[(size_t)i * nrhs + k] = acc;
-                    }
-                }
-                if (!waited) {
-                    // everything staged so far is independent of x: overlap it with the wait
-                    if (!wait_segment(a, s - 1)) return;
-                    waited = true;
-                } else {
-                    __syncthreads();
-                }
-                const bool narrow = bd.z != 0;
-                if (narrow && threadIdx.x >= 32) continue;  // warp 0 alone runs this block
-                for (int l = bd.x; l < bd.y; ++l) {
-                    const int64_t lp0 = a.lptr[l], lp1 = a.lptr[l + 1];
-                    const int64_t ring_lo = max(run_p0, lp1 - (int64_t)a.ring_rows);
-                    for (int64_t base = lp0; base < lp1; base += ngroups) {
-                        const int64_t p = base + grp;
-                        const bool act = p < lp1;
-                        const int i = (int)(p - P0);
-                        const int c0 = act ? s_cptr[i] : 0, c1 = act ? s_cptr[i + 1] : 0;
-                        for (int j = 0; j < ln.chunks; ++j) {
-                            const int k = ln.rl + j * ln.RL;
-                            const bool kv = act && k < nrhs;
-                            T acc = T(0);
-                            if (kv) {
-                                if (ln.el == 0) acc = s_bp[(size_t)i * nrhs + k];
-                                for (int q = c0 + ln.el; q < c1; q += ln.EL) {
-                                    const int32_t d = s_ccol[q];
-                                    const T xv = d >= ring_lo ? ring[(size_t)(d & ring_mask) * nrhs + k]
-                                                              : __ldcg(a.xp + (int64_t)d * nrhs + k);
-                                    acc -= s_cval[q] * xv;
-                                }
-                            }
-                            acc = group_reduce(acc, ln);
-                            if (kv && ln.el == 0) {
-                                ring[(size_t)(p & ring_mask) * nrhs + k] = acc;
-                                __stcg(a.xp + p * nrhs + k, acc);
-                                a.x[(int64_t)s_row[i] + (int64_t)k * a.ld] = acc;
-                            }
-                        }
-                    }
-                    if (narrow) __syncwarp();
-                    else __syncthreads();
-                    if (a.stamps && threadIdx.x == 0) a.stamps[l] = globaltimer();
-                }
-            }
+            RunSmem<T> sm;
+            sm.carve(smem, nrhs, RunGeom{a.ring_rows, a.stage_rows, a.stage_entries});
+            SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval, a.dinv,
+                         a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp};
+            auto wait = [&]() { return wait_segment(a, s - 1); };
+            if (!run_blocks(v, sm, ln, a.blocks, sg.y, sg.z, wait, a.stamps)) return;
             publish(a, s);
         }
     }
-}
-
-__global__ void k_gather_level_entries(const int32_t* lptr, const int32_t* cptr, int64_t m, int64_t* out) {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l <= m) out[l] = cptr[lptr[l]];
 }
 
 template <typename T>
@@ -290,6 +251,53 @@ int pow2_floor(int64_t v) {
 
 }  // namespace
 
+// Cuts levels [l_begin, l_end) into blocks that fit the staging area: whole levels while
+// they fit, a level that does not fit is split by rows.  Returns 0, or -1 when a single
+// row has more coefficients than the staging area holds.
+int build_run_blocks(const int32_t* lp, const int32_t* cptr, int64_t l_begin, int64_t l_end, int stage_rows,
+                     int stage_entries, int lpr, std::vector<int4>& out) {
+    int64_t P = lp[l_begin];
+    const int64_t Pend = lp[l_end];
+    int64_t l = l_begin;
+    while (P < Pend) {
+        while (lp[l + 1] <= P) ++l;
+        const int64_t P0 = P, l0 = l;
+        int64_t rows = 0, ents = 0, maxw = 0;
+        int64_t lcur = l;
+        while (P < Pend) {
+            while (lp[lcur + 1] <= P) ++lcur;
+            const int64_t lend = lp[lcur + 1];
+            const int64_t r = lend - P, e = (int64_t)cptr[lend] - cptr[P];
+            if (rows + r <= stage_rows && ents + e <= stage_entries) {
+                rows += r;
+                ents += e;
+                maxw = std::max(maxw, lend - std::max<int64_t>(lp[lcur], P0));
+                P = lend;
+                continue;
+            }
+            if (rows == 0) {
+                // this level alone does not fit: take the rows that do
+                int64_t q = P;
+                while (q < lend && rows + 1 <= stage_rows && ents + (cptr[q + 1] - cptr[q]) <= stage_entries) {
+                    ents += cptr[q + 1] - cptr[q];
+                    ++rows;
+                    ++q;
+                }
+                if (rows == 0) return -1;
+                maxw = rows;
+                P = q;
+            }
+            break;
+        }
+        int64_t l_last = l0;
+        while (lp[l_last + 1] < P) ++l_last;
+        const int nl = (int)(l_last - l0 + 1);
+        const int narrow = maxw * lpr <= 32 ? BLK_NARROW : 0;
+        out.push_back(make_int4((int)P0, (int)P, (int)l0, nl | narrow));
+    }
+    return 0;
+}
+
 sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     Schedule& sc = s->sched;
     const int vb = s->dtype == SPTRSV_F64 ? 8 : 4;
@@ -299,7 +307,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
         else lpr = (s->n > 0 && (double)s->nnz_c / (double)s->n > 12.0) ? 4 : 1;
     }
     int block = s->block > 0 ? s->block : 512;
-    block = std::max(32, std::min(1024, block / 32 * 32));
+    block = std::max(32, std::min(512, block / 32 * 32));
     if (lpr > 32 || (lpr & (lpr - 1))) {
         set_error("lanes per row must be a power of two <= 32");
         return SPTRSV_ERR_INVALID;
@@ -307,27 +315,21 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     if (sc.nrhs == nrhs && sc.lpr == lpr && sc.block == block && sc.run_width == s->run_width && sc.segs.p)
         return SPTRSV_OK;
     const int ngroups = block / lpr;
-    // shared memory: x ring (16 KB) + staging (32 KB)
-    int ring_rows = pow2_floor(std::max<int64_t>(16, 16384 / ((int64_t)nrhs * vb)));
+    // shared memory: staging (~32 KB) + an x ring of at least twice the staged rows
     int stage_entries = 1536;
-    int stage_rows = (int)((32768 - (int64_t)stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 8));
+    int stage_rows = (int)((32768 - (int64_t)stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
     if (stage_rows < 16) {
         stage_entries = 256;
-        stage_rows = std::max<int64_t>(16, (32768 - (int64_t)stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 8));
+        stage_rows = (int)std::max<int64_t>(16, (32768 - (int64_t)stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
     }
+    int ring_rows = 16;
+    while (ring_rows < 2 * stage_rows) ring_rows *= 2;
     int run_width = s->run_width > 0 ? s->run_width : (s->run_width < 0 ? 0 : ngroups);
     run_width = std::min(run_width, stage_rows);
     const int64_t m = s->m;
-    // entries per level (host copy)
-    std::vector<int64_t> lent(m + 1, 0);
-    if (m > 0) {
-        Scratch tmp;
-        SP_TRY(tmp.alloc((m + 1) * sizeof(int64_t), nullptr));
-        k_gather_level_entries<<<(unsigned)((m + 1 + 255) / 256), 256>>>(s->lv.level_ptr.p, s->cptr.p, m,
-                                                                         tmp.as<int64_t>());
-        SP_CUDA(cudaGetLastError());
-        SP_CUDA(cudaMemcpy(lent.data(), tmp.p, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
-    }
+    // row pointers of the stored coefficients (host copy) for cutting blocks
+    std::vector<int32_t> hcptr(s->n + 1, 0);
+    SP_CUDA(cudaMemcpy(hcptr.data(), s->cptr.p, (s->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
     const std::vector<int32_t>& lp = s->lv.h_level_ptr;
     sc.h_segs.clear();
     sc.h_blocks.clear();
@@ -335,8 +337,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     int64_t max_parts = 1;
     int sms = device_sm_count();
     // occupancy decides the number of CTAs that WIDE levels can be split over
-    size_t smem = (size_t)ring_rows * nrhs * vb + (size_t)stage_rows * nrhs * vb + (size_t)stage_entries * (vb + 4) +
-                  (size_t)(2 * stage_rows + 1) * 4;
+    size_t smem = run_smem_bytes(vb, nrhs, RunGeom{ring_rows, stage_rows, stage_entries});
     int occ = 0;
     if (s->dtype == SPTRSV_F64) {
         SP_CUDA(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -350,37 +351,24 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
         return SPTRSV_ERR_UNSUPPORTED;
     }
     const int64_t gmax = (int64_t)sms * occ;
+    auto thin = [&](int64_t l) {
+        return lp[l + 1] - lp[l] <= run_width && (int64_t)hcptr[lp[l + 1]] - hcptr[lp[l]] <= stage_entries;
+    };
     int64_t l = 0;
     while (l < m) {
-        int64_t w = lp[l + 1] - lp[l];
-        int64_t e = lent[l + 1] - lent[l];
-        bool thin = w <= run_width && e <= stage_entries;
-        if (thin) {
-            int blk0 = (int)sc.h_blocks.size();
+        if (thin(l)) {
             int64_t l1 = l;
-            while (l1 < m) {
-                int64_t w1 = lp[l1 + 1] - lp[l1];
-                int64_t e1 = lent[l1 + 1] - lent[l1];
-                if (!(w1 <= run_width && e1 <= stage_entries)) break;
-                // a block: consecutive thin levels within the staging capacity
-                int64_t b0 = l1, rows = 0, ents = 0, maxw = 0;
-                while (l1 < m) {
-                    int64_t w2 = lp[l1 + 1] - lp[l1];
-                    int64_t e2 = lent[l1 + 1] - lent[l1];
-                    if (!(w2 <= run_width && e2 <= stage_entries)) break;
-                    if (rows + w2 > stage_rows || ents + e2 > stage_entries) break;
-                    rows += w2;
-                    ents += e2;
-                    maxw = std::max(maxw, w2);
-                    ++l1;
-                }
-                int narrow = maxw * lpr <= 32 ? 1 : 0;
-                sc.h_blocks.push_back(make_int4((int)b0, (int)l1, narrow, 0));
+            while (l1 < m && thin(l1)) ++l1;
+            int blk0 = (int)sc.h_blocks.size();
+            if (build_run_blocks(lp.data(), hcptr.data(), l, l1, stage_rows, stage_entries, lpr, sc.h_blocks) != 0) {
+                set_error("schedule: a row has more coefficients than the staging area");
+                return SPTRSV_ERR_UNSUPPORTED;
             }
             sc.h_segs.push_back(make_int4(SEG_RUN, blk0, (int)sc.h_blocks.size(), 0));
             sc.run_levels += l1 - l;
             l = l1;
         } else {
+            int64_t w = lp[l + 1] - lp[l];
             int64_t per = std::max<int64_t>((w + gmax - 1) / gmax, ngroups);
             int64_t parts = (w + per - 1) / per;
             if (per >= INT32_MAX) { set_error("level too wide"); return SPTRSV_ERR_UNSUPPORTED; }
