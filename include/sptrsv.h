@@ -194,6 +194,22 @@ sptrsv_status sptrsv_solve(const sptrsv_system* s, const void* b_dev, void* x_de
 sptrsv_status sptrsv_solve_timed(const sptrsv_system* s, const void* b_dev, void* x_dev, int32_t nrhs, int64_t ld,
                                  uint64_t* stamps_dev, sptrsv_stream_t stream);
 
+/* A solve that allocates nothing, for callers that cannot allocate device memory when
+ * they solve: code running while a stream is captured into a CUDA graph, real-time
+ * loops that must stay out of the allocator, or processes whose memory a framework's
+ * caching allocator already holds.  (The paper has no counterpart; this is an interface
+ * of the library.)  Same arguments and result as sptrsv_solve; the solution scratch and
+ * the completion flags live in one fixed 64 MiB device array of the library, so
+ * n * nrhs * sizeof(value) must not exceed 64 MiB - 64 KiB (else SPTRSV_ERR_UNSUPPORTED).
+ * The system must already hold a solve schedule for this nrhs: call sptrsv_solve once
+ * with the same nrhs first (that call builds the schedule and may allocate); otherwise
+ * SPTRSV_ERR_INVALID.  The first call on a device looks up the array's device address
+ * and should come before any stream capture.  Every call on a device shares the array,
+ * so calls that overlap on the GPU race: order them on one stream.  The bounded-wait
+ * status goes to the system's status word (sptrsv_solve_status). */
+sptrsv_status sptrsv_solve_noalloc(const sptrsv_system* s, const void* b_dev, void* x_dev, int32_t nrhs, int64_t ld,
+                                   sptrsv_stream_t stream);
+
 /* Synchronizes the stream and reports the device status word of the system's last
  * solve (SPTRSV_OK or SPTRSV_ERR_TIMEOUT), then clears it. */
 sptrsv_status sptrsv_solve_status(const sptrsv_system* s, sptrsv_stream_t stream);

@@ -28,6 +28,7 @@ EXPORTED = [
     "sptrsv_last_error", "sptrsv_validate", "sptrsv_analyse", "sptrsv_levels_stats", "sptrsv_levels_export",
     "sptrsv_levels_destroy", "sptrsv_system_plain", "sptrsv_rewrite", "sptrsv_system_info_get",
     "sptrsv_system_export", "sptrsv_system_destroy", "sptrsv_solve", "sptrsv_solve_timed", "sptrsv_solve_status",
+    "sptrsv_solve_noalloc",
     "sptrsv_debug_set_wait", "sptrsv_system_tune", "sptrsv_batch_create", "sptrsv_batch_solve",
     "sptrsv_batch_info_get", "sptrsv_batch_destroy", "sptrsv_picker_create", "sptrsv_picker_destroy",
     "sptrsv_picker_get_params", "sptrsv_picker_set_params", "sptrsv_picker_set_norm", "sptrsv_picker_save",
@@ -98,6 +99,7 @@ def load():
             "sptrsv_solve": [vp, vp, vp, i32, i64, vp],
             "sptrsv_solve_timed": [vp, vp, vp, i32, i64, vp, vp],
             "sptrsv_solve_status": [vp, vp],
+            "sptrsv_solve_noalloc": [vp, vp, vp, i32, i64, vp],
             "sptrsv_debug_set_wait": [vp, i64, i64],
             "sptrsv_system_tune": [vp, i32, i32, i32],
             "sptrsv_batch_create": [vp, vp, i32, C.POINTER(vp), vp],
@@ -290,6 +292,12 @@ class System:
             check(load().sptrsv_solve_timed(self.h, _ptr(b), _ptr(x), nrhs, self.n, _ptr(stamps), _stream()))
         if check_status:
             self.status()
+        return x
+
+    def solve_noalloc(self, b, x):
+        """The solve that allocates nothing (x preallocated; schedule prepared by solve())."""
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        check(load().sptrsv_solve_noalloc(self.h, _ptr(b), _ptr(x), nrhs, self.n, _stream()))
         return x
 
     def status(self):
