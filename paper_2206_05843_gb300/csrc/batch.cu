@@ -49,10 +49,9 @@ __device__ void run_item(const BatchItem& it, const int4* blocks, const void* b,
                  (const T*)b,
                  (T*)x,
                  (T*)it.xp};
-    RunSmem<T> sm;
-    sm.carve(smem, it.nrhs, RunGeom{it.ring_rows, it.stage_rows, it.stage_entries});
     const Lanes ln = make_lanes(it.lpr, it.nrhs);
-    run_blocks(v, sm, ln, blocks, it.blk0, it.blk1, []() { return true; }, nullptr);
+    run_blocks(v, smem, RunGeom{it.ring_rows, it.stage_rows, it.stage_entries}, ln, blocks, it.blk0, it.blk1,
+               []() { return true; }, nullptr);
 }
 
 __global__ void __launch_bounds__(512) k_batch(const BatchItem* items, const int4* blocks, const int32_t* order,

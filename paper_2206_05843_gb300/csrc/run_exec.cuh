@@ -75,9 +75,13 @@ struct RunGeom {
     int ring_rows, stage_rows, stage_entries;
 };
 
+inline size_t run_stage_bytes(int vb, int nrhs, const RunGeom& g) {
+    return (size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) + (size_t)(3 * g.stage_rows + 2) * 4;
+}
+
+// the x ring plus two staging buffers (one is filled while the other is computed)
 inline size_t run_smem_bytes(int vb, int nrhs, const RunGeom& g) {
-    return (size_t)g.ring_rows * nrhs * vb + (size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) +
-           (size_t)(3 * g.stage_rows + 2) * 4;
+    return (size_t)g.ring_rows * nrhs * vb + 2 * ((run_stage_bytes(vb, nrhs, g) + 15) / 16 * 16);
 }
 
 template <typename T>
@@ -90,10 +94,14 @@ struct RunSmem {
     int32_t* row;
     int32_t* lp;
     RunGeom g;
-    __device__ void carve(unsigned char* base, int nrhs, RunGeom geo) {
+    // buffer 0 or 1 of the staging area; the ring is shared
+    __device__ void carve(unsigned char* base, int nrhs, RunGeom geo, int buf = 0) {
         g = geo;
         ring = (T*)base;
-        bp = ring + (size_t)g.ring_rows * nrhs;
+        const size_t vb = sizeof(T);
+        const size_t stage = ((size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) +
+                              (size_t)(3 * g.stage_rows + 2) * 4 + 15) / 16 * 16;
+        bp = (T*)(base + (size_t)g.ring_rows * nrhs * vb + buf * stage);
         cval = bp + (size_t)g.stage_rows * nrhs;
         cslot = (int32_t*)(cval + g.stage_entries);
         cptr = cslot + g.stage_entries;
@@ -109,16 +117,30 @@ struct RunSmem {
 constexpr int BLK_NARROW = 1 << 30;
 
 // stage A: rows, level pointers (relative to P0) and the b-part; thread per row
+// a group of threads that stages a block: all threads of the CTA (barrier 0) or the
+// warps after warp 0 (named barrier 1) while warp 0 computes the previous block
+struct Grp {
+    int tid, nthr, bar;
+    __device__ void sync() const {
+        if (bar == 0) __syncthreads();
+        else asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+    }
+};
+
+__device__ __forceinline__ Grp grp_all() { return Grp{(int)threadIdx.x, (int)blockDim.x, 0}; }
+__device__ __forceinline__ Grp grp_stagers() { return Grp{(int)threadIdx.x - 32, (int)blockDim.x - 32, 1}; }
+
 template <typename T>
-__device__ void run_stage_a(const SysView<T>& v, RunSmem<T>& sm, int l0, int nl, int64_t P0, int64_t P1) {
+__device__ void run_stage_a(const SysView<T>& v, RunSmem<T>& sm, int l0, int nl, int64_t P0, int64_t P1,
+                            const Grp& G) {
     const int nrhs = v.nrhs;
     const int rows = (int)(P1 - P0);
-    for (int li = threadIdx.x; li <= nl; li += blockDim.x) {
+    for (int li = G.tid; li <= nl; li += G.nthr) {
         int64_t q = li == nl ? P1 : (int64_t)v.lptr[l0 + li];
         q = q < P0 ? P0 : (q > P1 ? P1 : q);
         sm.lp[li] = (int32_t)(q - P0);
     }
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    for (int i = G.tid; i < rows; i += G.nthr) {
         const int64_t p = P0 + i;
         const int32_t row = v.perm[p];
         sm.row[i] = row;
@@ -130,10 +152,11 @@ __device__ void run_stage_a(const SysView<T>& v, RunSmem<T>& sm, int l0, int nl,
 // b-part; compact the others with their ring slots.  Same thread-to-row mapping as
 // stage A, so the b-part needs no barrier in between.
 template <typename T>
-__device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int rows, int64_t ring_lo) {
+__device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int rows, int64_t ring_lo,
+                            const Grp& G) {
     const int nrhs = v.nrhs;
     const int mask = sm.g.ring_rows - 1;
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    for (int i = G.tid; i < rows; i += G.nthr) {
         const int64_t p = P0 + i;
         const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
         int near = 0;
@@ -149,10 +172,10 @@ __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int
         }
         sm.cptr[i + 1] = near;
     }
-    __syncthreads();
-    // inclusive scan of the near counts by warp 0
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    G.sync();
+    // inclusive scan of the near counts by the group's first warp
+    if (G.tid < 32) {
+        const int lane = G.tid;
         int carry = 0;
         for (int base = 0; base < rows; base += 32) {
             const int i = base + lane;
@@ -167,8 +190,8 @@ __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int
         }
         if (lane == 0) sm.cptr[0] = 0;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    G.sync();
+    for (int i = G.tid; i < rows; i += G.nthr) {
         const int64_t p = P0 + i;
         const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
         int o = sm.cptr[i];
@@ -181,7 +204,7 @@ __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int
             }
         }
     }
-    __syncthreads();
+    G.sync();
 }
 
 // Narrow block, one right-hand side, one lane per row: the coefficients and ring slots of
@@ -287,28 +310,55 @@ __device__ void run_write_out(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, i
     }
 }
 
-// runs blocks [blk0, blk1); `wait` is called once, after the first block's stage A
+// Runs blocks [blk0, blk1).  `wait` is called once, after the first block's stage A.
+// Iteration of block i: compute block i (buffer i % 2) while -- when block i is narrow and
+// single-RHS -- warps 1.. stage block i+1 into the other buffer; then every thread writes
+// block i's x out of the ring.  Block i+1's stage B reads x only of blocks <= i-1 (a
+// dependency inside block i is always inside the ring window), which iteration i-1
+// wrote out.
 template <typename T, typename WaitFn>
-__device__ bool run_blocks(const SysView<T>& v, RunSmem<T>& sm, const Lanes& ln, const int4* blocks, int blk0,
-                           int blk1, WaitFn wait, unsigned long long* stamps) {
+__device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo, const Lanes& ln, const int4* blocks,
+                           int blk0, int blk1, WaitFn wait, unsigned long long* stamps) {
     if (blk0 >= blk1) return wait();
     const int64_t run_p0 = blocks[blk0].x;
-    for (int blk = blk0; blk < blk1; ++blk) {
-        const int4 bd = blocks[blk];
-        const int64_t P0 = bd.x, P1 = bd.y;
-        const int nl = bd.w & (BLK_NARROW - 1);
-        const int rows = (int)(P1 - P0);
-        __syncthreads();  // the previous block is done with shared memory and has written x
-        run_stage_a(v, sm, bd.z, nl, P0, P1);
-        if (blk == blk0 && !wait()) return false;
-        const int64_t ring_lo = max(run_p0, P1 - (int64_t)sm.g.ring_rows);
-        run_stage_b(v, sm, P0, rows, ring_lo);
-        if ((bd.w & BLK_NARROW) && v.nrhs == 1 && ln.lpr == 1)
-            run_compute_narrow1(sm, P0, bd.z, nl, stamps);
-        else
-            run_compute(v, sm, ln, (bd.w & BLK_NARROW) != 0, P0, bd.z, nl, stamps);
+    const int R = geo.ring_rows;
+    {
+        RunSmem<T> s0;
+        s0.carve(smem, v.nrhs, geo, 0);
+        const int4 bd = blocks[blk0];
         __syncthreads();
-        run_write_out(v, sm, P0, rows);
+        run_stage_a(v, s0, bd.z, bd.w & (BLK_NARROW - 1), bd.x, bd.y, grp_all());
+        if (!wait()) return false;
+        run_stage_b(v, s0, bd.x, bd.y - bd.x, max(run_p0, (int64_t)bd.y - R), grp_all());
+    }
+    for (int blk = blk0; blk < blk1; ++blk) {
+        const int par = (blk - blk0) & 1;
+        RunSmem<T> cur;
+        cur.carve(smem, v.nrhs, geo, par);
+        const int4 bd = blocks[blk];
+        const int64_t P0 = bd.x;
+        const int nl = bd.w & (BLK_NARROW - 1);
+        const bool narrow = (bd.w & BLK_NARROW) != 0;
+        const bool next = blk + 1 < blk1;
+        const bool fast = narrow && v.nrhs == 1 && ln.lpr == 1;
+        const bool overlap = fast && next && blockDim.x > 32;
+        if (!overlap || threadIdx.x < 32) {
+            if (fast) run_compute_narrow1(cur, P0, bd.z, nl, stamps);
+            else run_compute(v, cur, ln, narrow, P0, bd.z, nl, stamps);
+        }
+        if (!overlap) __syncthreads();
+        if (next && (!overlap || threadIdx.x >= 32)) {
+            // stage the next block into the other buffer
+            RunSmem<T> nx;
+            nx.carve(smem, v.nrhs, geo, par ^ 1);
+            const int4 bn = blocks[blk + 1];
+            const Grp G = overlap ? grp_stagers() : grp_all();
+            run_stage_a(v, nx, bn.z, bn.w & (BLK_NARROW - 1), bn.x, bn.y, G);
+            run_stage_b(v, nx, bn.x, bn.y - bn.x, max(run_p0, (int64_t)bn.y - R), G);
+        }
+        if (overlap) __syncthreads();
+        run_write_out(v, cur, P0, (int)(bd.y - bd.x));
+        __syncthreads();
     }
     return true;
 }

@@ -180,12 +180,12 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
             if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
         } else {
             if (me != 0) continue;
-            RunSmem<T> sm;
-            sm.carve(smem, nrhs, RunGeom{a.ring_rows, a.stage_rows, a.stage_entries});
             SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval, a.dinv,
                          a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp};
             auto wait = [&]() { return wait_segment(a, s - 1); };
-            if (!run_blocks(v, sm, ln, a.blocks, sg.y, sg.z, wait, a.stamps)) return;
+            if (!run_blocks(v, smem, RunGeom{a.ring_rows, a.stage_rows, a.stage_entries}, ln, a.blocks, sg.y, sg.z,
+                            wait, a.stamps))
+                return;
             publish(a, s);
         }
     }
