@@ -120,12 +120,14 @@ enum {
     SPTRSV_STRATEGY_NAIVE = 1,   /* Section III avgLevelCost strategy over thin levels */
     SPTRSV_STRATEGY_DEPTH_K = 2, /* fixed distance: each target takes the next k levels (Section III, manual approach) */
     SPTRSV_STRATEGY_LEARNED = 3, /* depth per target chosen by a trained picker (falls back to NAIVE without one) */
-    SPTRSV_STRATEGY_CHOSEN = 4   /* depth per target given by the caller */
+    SPTRSV_STRATEGY_CHOSEN = 4,  /* depth per target given by the caller */
+    SPTRSV_STRATEGY_MANUAL = 5   /* fixed distance k over thin levels only: the manual approach of the earlier work
+                                    ("every 9 levels into the 10th", Sections III and IV) */
 };
 
 typedef struct {
     int32_t kind;                  /* SPTRSV_STRATEGY_* */
-    int32_t k;                     /* DEPTH_K: levels merged into each target */
+    int32_t k;                     /* DEPTH_K / MANUAL: levels merged into each target */
     double nnz_growth_cap;         /* > 0: nnz(L') + nnz(E) <= cap * nnz(L); <= 0: no cap */
     double avg_override;           /* > 0: use this avgLevelCost instead of the computed one */
     double growth_guard;           /* > 0: fail with SPTRSV_ERR_NUMERIC if a rewritten coefficient exceeds it in magnitude */
@@ -220,8 +222,32 @@ sptrsv_status sptrsv_solve_status(const sptrsv_system* s, sptrsv_stream_t stream
 sptrsv_status sptrsv_debug_set_wait(sptrsv_system* s, int64_t withhold_segment, int64_t timeout_ns);
 
 /* Tuning knobs of one system (0 keeps the current value): block size of the persistent
- * kernel, widest level executed inside a single-CTA run, lanes per row. */
+ * kernel, widest level executed inside a single-CTA run (-1: no runs; -2: no persistent
+ * kernel at all, one launch of a row-per-thread kernel per level), lanes per row. */
 sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_width, int32_t lanes_per_row);
+
+/* Autotuner: times candidate solves (b = 0) over lanes per row and the widest level
+ * executed inside a single-CTA run, keeps the fastest for nrhs right-hand sides and
+ * caches the choice by the system's signature (n, m, stored entries, nrhs, dtype).
+ * *best_us_host (may be NULL) receives the best time.  Synchronizes the stream. */
+sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, double* best_us_host, sptrsv_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
+ * Upper-triangular systems U x = b (the second triangular solve of an ILU preconditioner,
+ * Section I), through the index reversal i -> n-1-i
+ * ------------------------------------------------------------------------------- */
+
+/* Writes the lower-triangular matrix of the reversed index order of U (CSR, columns
+ * ascending, diagonal FIRST in each row) into caller device buffers of the same sizes:
+ * rowptr (n+1), colidx (nnz), vals (nnz, U's dtype).  The result satisfies the CSR
+ * contract of sptrsv_analyse when U is upper triangular with a non-zero diagonal (that
+ * call validates it).  Stream-ordered. */
+sptrsv_status sptrsv_upper_to_lower(const sptrsv_csr* U, int32_t* rowptr_dev, int32_t* colidx_dev, void* vals_dev,
+                                    sptrsv_stream_t stream);
+
+/* Re-indexes a system built from the reversed matrix so that it solves U x = b with b and
+ * x in U's numbering (and its exports use that numbering).  Synchronizes the stream. */
+sptrsv_status sptrsv_system_reverse_rows(sptrsv_system* s, sptrsv_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
  * Batched solve

@@ -25,7 +25,7 @@ _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NAIVE, DEPTH, CHOSEN = 1, 2, 3
+NAIVE, DEPTH, CHOSEN, MANUAL = 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -52,6 +52,8 @@ def _load():
         lib.orc_forward_subst.restype = None
         lib.orc_forward_subst_f32vals.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.orc_forward_subst_f32vals.restype = None
+        lib.orc_backward_subst.argtypes = [i64, vp, vp, vp, vp, vp]
+        lib.orc_backward_subst.restype = None
         lib.orc_levels.argtypes = [i64, vp, vp, C.c_int, vp]
         lib.orc_levels.restype = i32
         lib.orc_level_stats.argtypes = [i64, vp, vp, i32, vp, vp, vp]
@@ -124,6 +126,22 @@ def forward_subst(rowptr, colidx, vals, b) -> np.ndarray:
     return X[0] if one else X
 
 
+def backward_subst(rowptr, colidx, vals, b) -> np.ndarray:
+    """x = U^{-1} b for an upper-triangular CSR U with the diagonal first in each row."""
+    lib = _load()
+    rp, ci, v = _i32(rowptr), _i32(colidx), _f64(vals)
+    b = _f64(b)
+    one = b.ndim == 1
+    B = b[None, :] if one else b
+    X = np.empty_like(B)
+    n = rp.size - 1
+    for k in range(B.shape[0]):
+        bk, xk = np.ascontiguousarray(B[k]), np.empty(n)
+        lib.orc_backward_subst(n, _p(rp), _p(ci), _p(v), _p(bk), _p(xk))
+        X[k] = xk
+    return X[0] if one else X
+
+
 def levels(rowptr, colidx, diag_last: bool = True) -> tuple[np.ndarray, int]:
     """(level[n], m) by the definition level(i) = 1 + max level of its dependencies."""
     rp, ci = _i32(rowptr), _i32(colidx)
@@ -156,7 +174,7 @@ class Plan:
 
 def plan(rowptr, colidx, level, m, kind: int, k: int = 0, avg: float = 0.0, cap: float = 0.0,
          injected_cost=None, depth_of_target=None) -> Plan:
-    """The Section III planner (NAIVE / DEPTH / CHOSEN); see sptrsv_oracle.c."""
+    """The Section III planner (NAIVE / DEPTH / CHOSEN / MANUAL); see sptrsv_oracle.c."""
     rp, ci, lv = _i32(rowptr), _i32(colidx), _i32(level)
     n = rp.size - 1
     tgt = np.empty(max(n, 1), np.int32)

@@ -168,6 +168,8 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
 #define ORC_NAIVE 1   /* avgLevelCost over thin levels */
 #define ORC_DEPTH 2   /* fixed distance: target every (k+1)-th level, k levels merged in */
 #define ORC_CHOSEN 3  /* per-target depth given by the caller (learned picker) */
+#define ORC_MANUAL 4  /* fixed distance over thin levels only: "every 9 levels into the 10th"
+                         applied to the levels cheaper than avgLevelCost (Section IV) */
 
 /*
  * Walk the levels in order and decide, row by row, the level each row moves to.
@@ -193,6 +195,8 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
  * DEPTH / CHOSEN: every level is eligible; a level s joins target t while
  *   s - t <= depth(t) (depth k for DEPTH, depth_of_target[t] for CHOSEN), otherwise s
  *   becomes the next target.  The nnz cap rejects rows as in NAIVE.
+ * MANUAL: thin levels are eligible as in NAIVE, levels join a target by distance as in
+ *   DEPTH (no cost rule).
  *
  * inputs : lower-triangular CSR (diagonal last), level[n], m, kind, k, avg_override
  *          (<= 0: computed), cap_ratio (<= 0: no cap), injected_cost (NULL: computed),
@@ -247,10 +251,10 @@ int orc_plan(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int3
     int32_t t = -1;
     int64_t cur = 0;
     for (int32_t s = 0; s < m; ++s) {
-        int eligible = (kind == ORC_NAIVE) ? ((double)lcost[s] < avg) : 1;
+        int eligible = (kind == ORC_NAIVE || kind == ORC_MANUAL) ? ((double)lcost[s] < avg) : 1;
         if (!eligible) { t = -1; continue; }
         if (t < 0) { t = s; cur = lcost[s]; targets++; continue; }
-        if (kind == ORC_DEPTH && s - t > k) { t = s; cur = lcost[s]; targets++; continue; }
+        if ((kind == ORC_DEPTH || kind == ORC_MANUAL) && s - t > k) { t = s; cur = lcost[s]; targets++; continue; }
         if (kind == ORC_CHOSEN && s - t > depth_of_target[t]) { t = s; cur = lcost[s]; targets++; continue; }
         for (int64_t q = lptr[s]; q < lptr[s + 1]; ++q) {
             int64_t r = byl[q];
@@ -524,5 +528,20 @@ void orc_solve_rewritten(const orc_system* s, const double* b, double* x) {
         double sum = 0.0;
         for (int64_t q = s->cptr[r]; q < s->cptr[r + 1]; ++q) sum += s->cval[q] * x[s->ccol[q]];
         x[r] = (rhs - sum) / s->dval[r];
+    }
+}
+
+/* ------------------------------------------------------------------------------- */
+/* backward substitution (upper-triangular U x = b, diagonal FIRST in each row)      */
+/* ------------------------------------------------------------------------------- */
+
+/* x_i = (b_i - sum_{j>i} U_ij x_j) / U_ii for i = n-1 down to 0. */
+void orc_backward_subst(int64_t n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
+                        const double* b, double* x) {
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double sum = 0.0;
+        int64_t first = rowptr[i];
+        for (int64_t j = first + 1; j < rowptr[i + 1]; ++j) sum += vals[j] * x[colidx[j]];
+        x[i] = (b[i] - sum) / vals[first];
     }
 }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsptrsv.so")
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNSUPPORTED"}
 F64, F32 = 0, 1
-NONE, NAIVE, DEPTH_K, LEARNED, CHOSEN = 0, 1, 2, 3, 4
+NONE, NAIVE, DEPTH_K, LEARNED, CHOSEN, MANUAL = 0, 1, 2, 3, 4, 5
 PICKER_FEATURES, PICKER_HIDDEN = 12, 64
 PICKER_PARAMS = 12 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 
@@ -28,7 +28,7 @@ EXPORTED = [
     "sptrsv_last_error", "sptrsv_validate", "sptrsv_analyse", "sptrsv_levels_stats", "sptrsv_levels_export",
     "sptrsv_levels_destroy", "sptrsv_system_plain", "sptrsv_rewrite", "sptrsv_system_info_get",
     "sptrsv_system_export", "sptrsv_system_destroy", "sptrsv_solve", "sptrsv_solve_timed", "sptrsv_solve_status",
-    "sptrsv_solve_noalloc",
+    "sptrsv_solve_noalloc", "sptrsv_system_autotune", "sptrsv_upper_to_lower", "sptrsv_system_reverse_rows",
     "sptrsv_debug_set_wait", "sptrsv_system_tune", "sptrsv_batch_create", "sptrsv_batch_solve",
     "sptrsv_batch_info_get", "sptrsv_batch_destroy", "sptrsv_picker_create", "sptrsv_picker_destroy",
     "sptrsv_picker_get_params", "sptrsv_picker_set_params", "sptrsv_picker_set_norm", "sptrsv_picker_save",
@@ -102,6 +102,9 @@ def load():
             "sptrsv_solve_noalloc": [vp, vp, vp, i32, i64, vp],
             "sptrsv_debug_set_wait": [vp, i64, i64],
             "sptrsv_system_tune": [vp, i32, i32, i32],
+            "sptrsv_system_autotune": [vp, i32, vp, vp],
+            "sptrsv_upper_to_lower": [vp, vp, vp, vp, vp],
+            "sptrsv_system_reverse_rows": [vp, vp],
             "sptrsv_batch_create": [vp, vp, i32, C.POINTER(vp), vp],
             "sptrsv_batch_solve": [vp, vp, vp, vp],
             "sptrsv_batch_info_get": [vp, vp],
@@ -191,6 +194,25 @@ class Matrix:
         check(load().sptrsv_validate(C.byref(self.csr), _stream()))
 
 
+def upper_to_lower(U: "Matrix") -> "Matrix":
+    """The lower-triangular matrix of the reversed index order of an upper-triangular U
+    (diagonal first in each row), computed on the device."""
+    torch = _torch()
+    rp = torch.empty_like(U.rowptr)
+    ci = torch.empty_like(U.colidx)
+    va = torch.empty_like(U.vals)
+    check(load().sptrsv_upper_to_lower(C.byref(U.csr), _ptr(rp), _ptr(ci), _ptr(va), _stream()))
+    return Matrix(U.n, rp, ci, va)
+
+
+def solve_upper(U: "Matrix", b, kind=NONE, **kw):
+    """x = U^{-1} b through the reversed lower-triangular system (plain or rewritten)."""
+    L = upper_to_lower(U)
+    lv = Levels(L)
+    s = System(L, lv, kind, **kw).reverse_rows()
+    return s.solve(b, check_status=True), s, (L, lv)
+
+
 class Levels:
     def __init__(self, matrix: Matrix):
         h = C.c_void_p()
@@ -276,6 +298,18 @@ class System:
 
     def tune(self, block=0, run_width=0, lanes_per_row=0):
         check(load().sptrsv_system_tune(self.h, block, run_width, lanes_per_row))
+
+    def autotune(self, nrhs=1) -> float:
+        """Times candidate schedules and keeps the fastest; returns its time in us."""
+        us = C.c_double(0)
+        check(load().sptrsv_system_autotune(self.h, nrhs, C.byref(us), _stream()))
+        self.refresh()
+        return us.value
+
+    def reverse_rows(self):
+        """Re-index a system built from upper_to_lower(U) so that it solves U x = b."""
+        check(load().sptrsv_system_reverse_rows(self.h, _stream()))
+        return self
 
     def debug_set_wait(self, withhold_segment=-1, timeout_ns=0):
         check(load().sptrsv_debug_set_wait(self.h, withhold_segment, timeout_ns))

@@ -22,7 +22,7 @@
 namespace sp {
 
 // kinds of the walk
-enum { WALK_NAIVE = 1, WALK_DEPTH = 2, WALK_CHOSEN = 3 };
+enum { WALK_NAIVE = 1, WALK_DEPTH = 2, WALK_CHOSEN = 3, WALK_MANUAL = 4 };
 
 namespace {
 
@@ -38,16 +38,43 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
     return v;
 }
 
-// insertion sort + unique of an int32 range in global memory; returns the new length
-__device__ int sort_unique(int32_t* a, int len) {
-    for (int i = 1; i < len; ++i) {
-        int32_t v = a[i];
-        int j = i - 1;
-        while (j >= 0 && a[j] > v) {
-            a[j + 1] = a[j];
-            --j;
+// in-place heap sort of an int32 range (rows of the planner can hold thousands of entries)
+__device__ void heap_sort_i32(int32_t* a, int n) {
+    auto sift = [&](int root, int end) {
+        while (true) {
+            int child = 2 * root + 1;
+            if (child >= end) break;
+            if (child + 1 < end && a[child] < a[child + 1]) ++child;
+            if (a[root] >= a[child]) break;
+            int32_t t = a[root];
+            a[root] = a[child];
+            a[child] = t;
+            root = child;
         }
-        a[j + 1] = v;
+    };
+    for (int i = n / 2 - 1; i >= 0; --i) sift(i, n);
+    for (int end = n - 1; end > 0; --end) {
+        int32_t t = a[0];
+        a[0] = a[end];
+        a[end] = t;
+        sift(0, end);
+    }
+}
+
+// sort + unique of an int32 range in global memory; returns the new length
+__device__ int sort_unique(int32_t* a, int len) {
+    if (len <= 32) {
+        for (int i = 1; i < len; ++i) {
+            int32_t v = a[i];
+            int j = i - 1;
+            while (j >= 0 && a[j] > v) {
+                a[j + 1] = a[j];
+                --j;
+            }
+            a[j + 1] = v;
+        }
+    } else {
+        heap_sort_i32(a, len);
     }
     int w = 0;
     for (int i = 0; i < len; ++i)
@@ -87,12 +114,13 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
     int64_t cur = 0, stored = a.nnzL, moved = 0, targets = 0, top = 0;
     for (int64_t s = 0; s < a.m; ++s) {
         const int64_t ls = a.lcost[s];
-        const bool eligible = a.kind == WALK_NAIVE ? ((double)ls < a.avg) : true;
+        const bool eligible = (a.kind == WALK_NAIVE || a.kind == WALK_MANUAL) ? ((double)ls < a.avg) : true;
         if (!eligible) {
             t = -1;
             continue;
         }
-        if (t < 0 || (a.kind == WALK_DEPTH && s - t > a.k) || (a.kind == WALK_CHOSEN && s - t > a.dot[t])) {
+        if (t < 0 || ((a.kind == WALK_DEPTH || a.kind == WALK_MANUAL) && s - t > a.k) ||
+            (a.kind == WALK_CHOSEN && s - t > a.dot[t])) {
             t = (int)s;
             cur = ls;
             targets++;
@@ -254,6 +282,8 @@ struct FillArgs {
     double* hval;
     int64_t* ub;  // per row: upper bound of C + E entries this round (0 for other rows)
     int64_t* ubc;
+    int32_t* tcol;  // per-round temporary of the merge sort (same offsets as the round's rows)
+    double* tval;
     double guard;
     int* status;
 };
@@ -281,19 +311,42 @@ __global__ void k_fill_size(FillArgs<T> a, int d) {
     a.ubc[r] = uc;
 }
 
-// stable insertion sort of (col, val) pairs by col, then sum equal columns in order
-__device__ int sort_merge(int32_t* c, double* v, int len) {
-    for (int i = 1; i < len; ++i) {
-        int32_t ci = c[i];
-        double vi = v[i];
-        int j = i - 1;
-        while (j >= 0 && c[j] > ci) {
-            c[j + 1] = c[j];
-            v[j + 1] = v[j];
-            --j;
+// Stable sort of (col, val) pairs by col -- insertion sort for short rows, a bottom-up
+// merge sort through the temporary arrays for long ones -- then equal columns are summed
+// in their original order (the order the serial rewrite adds them in).
+__device__ int sort_merge(int32_t* c, double* v, int32_t* tc, double* tv, int len) {
+    if (len <= 32) {
+        for (int i = 1; i < len; ++i) {
+            int32_t ci = c[i];
+            double vi = v[i];
+            int j = i - 1;
+            while (j >= 0 && c[j] > ci) {
+                c[j + 1] = c[j];
+                v[j + 1] = v[j];
+                --j;
+            }
+            c[j + 1] = ci;
+            v[j + 1] = vi;
         }
-        c[j + 1] = ci;
-        v[j + 1] = vi;
+    } else {
+        int32_t *sc = c, *dc = tc;
+        double *sv = v, *dv = tv;
+        for (int w = 1; w < len; w *= 2) {
+            for (int lo = 0; lo < len; lo += 2 * w) {
+                const int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
+                int i = lo, j = mid, o = lo;
+                while (i < mid && j < hi) {
+                    if (sc[j] < sc[i]) { dc[o] = sc[j]; dv[o++] = sv[j++]; }
+                    else { dc[o] = sc[i]; dv[o++] = sv[i++]; }
+                }
+                while (i < mid) { dc[o] = sc[i]; dv[o++] = sv[i++]; }
+                while (j < hi) { dc[o] = sc[j]; dv[o++] = sv[j++]; }
+            }
+            int32_t* t1 = sc; sc = dc; dc = t1;
+            double* t2 = sv; sv = dv; dv = t2;
+        }
+        if (sc != c)
+            for (int i = 0; i < len; ++i) { c[i] = sc[i]; v[i] = sv[i]; }
     }
     int w = 0;
     for (int i = 0; i < len; ++i) {
@@ -358,8 +411,10 @@ __global__ void k_fill(FillArgs<T> a, int d, const int64_t* off, int64_t heap_ba
             ev[ne++] = __ddiv_rn(-aj, dj);
         }
     }
-    nc = sort_merge(cc, cv, nc);
-    ne = sort_merge(ec, ev, ne);
+    int32_t* tc = a.tcol + off[r];
+    double* tv = a.tval + off[r];
+    nc = sort_merge(cc, cv, tc, tv, nc);
+    ne = sort_merge(ec, ev, tc + uc, tv + uc, ne);
     bool bad = false;
     for (int i = 0; i < nc; ++i) {
         cv[i] = __ddiv_rn(cv[i], drr);
@@ -416,7 +471,7 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
                            double avg, double cap, const int64_t* inj, int32_t* target, PlanOut& po,
                            cudaStream_t st) {
     const int64_t n = L->n, m = lv.m;
-    const bool walk = kind == WALK_NAIVE || cap > 0 || inj;
+    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || cap > 0 || inj;
     if (!walk) {
         Scratch lt;
         SP_TRY(lt.alloc(std::max<int64_t>(1, m) * sizeof(int32_t), st));
@@ -433,7 +488,7 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
     SP_TRY(elen.alloc(n * 4, st));
     SP_TRY(info.alloc(4 * 8, st));
     SP_TRY(status.alloc(sizeof(int), st));
-    int64_t cap_pool = std::max<int64_t>(1 << 20, 2 * L->nnz);
+    int64_t cap_pool = std::max<int64_t>(1 << 22, (cap > 0 ? 2 : 16) * L->nnz);
     for (int attempt = 0; attempt < 6; ++attempt) {
         Scratch pool;
         SP_TRY(pool.alloc((size_t)cap_pool * sizeof(int32_t), st));
@@ -562,6 +617,11 @@ sptrsv_status rewrite_rows(const sptrsv_csr* L, const Levels& lv, const int32_t*
         }
         a.hcol = hcol.p;
         a.hval = hval.p;
+        Scratch tcol, tval;
+        SP_TRY(tcol.alloc(std::max<int64_t>(1, tot) * sizeof(int32_t), st));
+        SP_TRY(tval.alloc(std::max<int64_t>(1, tot) * sizeof(double), st));
+        a.tcol = tcol.as<int32_t>();
+        a.tval = tval.as<double>();
         k_fill<T><<<nblk(n, 128), 128, 0, st>>>(a, d, off.as<int64_t>(), heap_top);
         SP_CUDA(cudaGetLastError());
         heap_top += tot;
@@ -673,7 +733,10 @@ extern "C" sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels
             return learned_rewrite(L, lvh, sg, out, st);
         }
     }
-    if (kind == SPTRSV_STRATEGY_DEPTH_K && sg->k < 0) { set_error("rewrite: depth k < 0"); return SPTRSV_ERR_INVALID; }
+    if ((kind == SPTRSV_STRATEGY_DEPTH_K || kind == SPTRSV_STRATEGY_MANUAL) && sg->k < 0) {
+        set_error("rewrite: depth k < 0");
+        return SPTRSV_ERR_INVALID;
+    }
     Scratch dot;
     const int32_t* dot_dev = nullptr;
     if (kind == SPTRSV_STRATEGY_CHOSEN) {
@@ -683,7 +746,7 @@ extern "C" sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels
         dot_dev = dot.as<int32_t>();
     }
     int wk = kind == SPTRSV_STRATEGY_NAIVE ? WALK_NAIVE : kind == SPTRSV_STRATEGY_DEPTH_K ? WALK_DEPTH
-           : kind == SPTRSV_STRATEGY_CHOSEN ? WALK_CHOSEN : 0;
+           : kind == SPTRSV_STRATEGY_CHOSEN ? WALK_CHOSEN : kind == SPTRSV_STRATEGY_MANUAL ? WALK_MANUAL : 0;
     if (!wk) { set_error("rewrite: unknown strategy %d", kind); return SPTRSV_ERR_INVALID; }
     return rewrite_system(L, lv, wk, sg->k, dot_dev, sg->avg_override, sg->nnz_growth_cap, sg->growth_guard,
                           sg->injected_cost_dev, out, st);

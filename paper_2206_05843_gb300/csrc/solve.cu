@@ -9,6 +9,10 @@
 // block by block, x of the run stays in a shared-memory ring, and consecutive levels are
 // separated by a CTA (or warp) barrier instead of a device-wide handoff.
 #include <algorithm>
+#include <map>
+#include <tuple>
+#include <mutex>
+#include <vector>
 
 #include "solve_kernel.cuh"
 
@@ -50,6 +54,17 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
 
     SP_CUDA(cudaMemsetAsync(s->flags.p, 0xff, (size_t)sc.grid * sizeof(int), st));
     SP_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
+    if (s->run_width == -2) {
+        // one launch per level
+        const std::vector<int32_t>& lp = s->lv.h_level_ptr;
+        for (int64_t l = 0; l < s->m; ++l) {
+            const int64_t rows = (int64_t)(lp[l + 1] - lp[l]) * nrhs;
+            k_level<T><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a, lp[l], lp[l + 1]);
+            if (stamps) k_stamp<<<1, 32, 0, st>>>(stamps, l);
+        }
+        SP_CUDA(cudaGetLastError());
+        return SPTRSV_OK;
+    }
     if (a.nseg == 0) return SPTRSV_OK;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)sc.grid);
@@ -150,8 +165,11 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     run_width = std::min(run_width, stage_rows);
     const int64_t m = s->m;
     // row pointers of the stored coefficients (host copy) for cutting blocks
-    std::vector<int32_t> hcptr(s->n + 1, 0);
-    SP_CUDA(cudaMemcpy(hcptr.data(), s->cptr.p, (s->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if ((int64_t)s->h_cptr.size() != s->n + 1) {
+        s->h_cptr.assign(s->n + 1, 0);
+        SP_CUDA(cudaMemcpy(s->h_cptr.data(), s->cptr.p, (s->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    }
+    const std::vector<int32_t>& hcptr = s->h_cptr;
     const std::vector<int32_t>& lp = s->lv.h_level_ptr;
     sc.h_segs.clear();
     sc.h_blocks.clear();
@@ -234,3 +252,109 @@ sptrsv_status enqueue_solve(sptrsv_system* s, const void* b, void* x, int nrhs, 
 }
 
 }  // namespace sp
+
+namespace sp {
+namespace {
+struct TuneKey {
+    int64_t n, m, nnz_c, nnz_e;
+    int nrhs, dtype;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(n, m, nnz_c, nnz_e, nrhs, dtype) < std::tie(o.n, o.m, o.nnz_c, o.nnz_e, o.nrhs, o.dtype);
+    }
+};
+struct TuneVal {
+    int block, run_width, lpr;
+    double us;
+};
+std::mutex g_stune_mu;
+std::map<TuneKey, TuneVal> g_stune_cache;
+}  // namespace
+}  // namespace sp
+
+extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, double* best_us,
+                                                sptrsv_stream_t stream) {
+    using namespace sp;
+    if (!s || nrhs < 1) { set_error("system_autotune: bad argument"); return SPTRSV_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->n == 0) {
+        if (best_us) *best_us = 0;
+        return SPTRSV_OK;
+    }
+    const TuneKey key{s->n, s->m, s->nnz_c, s->nnz_e, nrhs, s->dtype};
+    {
+        std::lock_guard<std::mutex> lk(g_stune_mu);
+        auto f = g_stune_cache.find(key);
+        if (f != g_stune_cache.end()) {
+            s->block = f->second.block;
+            s->run_width = f->second.run_width;
+            s->lpr = f->second.lpr;
+            if (best_us) *best_us = f->second.us;
+            return prepare_schedule(s, nrhs);
+        }
+    }
+    const size_t vb = s->dtype == SPTRSV_F64 ? 8 : 4;
+    Scratch b, x;
+    SP_TRY(b.alloc((size_t)s->n * nrhs * vb, st));
+    SP_TRY(x.alloc((size_t)s->n * nrhs * vb, st));
+    SP_CUDA(cudaMemsetAsync(b.p, 0, (size_t)s->n * nrhs * vb, st));
+    std::vector<int> lprs;
+    if (nrhs == 1) lprs = {1, 2, 4};
+    else {
+        int p = 1;
+        while (p < nrhs && p < 32) p <<= 1;
+        lprs = {std::max(1, p / 2), p};
+    }
+    std::vector<int> widths = {0, 64, -1};
+    if (s->m <= 256) widths.push_back(-2);  // one launch per level
+    cudaEvent_t e0, e1;
+    SP_CUDA(cudaEventCreate(&e0));
+    SP_CUDA(cudaEventCreate(&e1));
+    TuneVal best{512, 0, 0, 1e300};
+    const int old_block = s->block, old_rw = s->run_width, old_lpr = s->lpr;
+    sptrsv_status rc = SPTRSV_OK;
+    for (int lpr : lprs) {
+        for (int rw : widths) {
+            if (rw == -2 && lpr != lprs[0]) continue;
+            s->block = 512;
+            s->run_width = rw;
+            s->lpr = lpr;
+            s->sched.nrhs = -1;
+            rc = enqueue_solve(s, b.p, x.p, nrhs, s->n, nullptr, st);
+            if (rc != SPTRSV_OK) break;
+            float bestms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = enqueue_solve(s, b.p, x.p, nrhs, s->n, nullptr, st);
+                cudaEventRecord(e1, st);
+                if (rc != SPTRSV_OK) break;
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                bestms = std::min(bestms, ms);
+            }
+            if (rc != SPTRSV_OK) break;
+            if (bestms * 1e3 < best.us) best = TuneVal{512, rw, lpr, bestms * 1e3};
+        }
+        if (rc != SPTRSV_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SPTRSV_OK) {
+        s->block = old_block;
+        s->run_width = old_rw;
+        s->lpr = old_lpr;
+        s->sched.nrhs = -1;
+        return rc;
+    }
+    SP_TRY(sptrsv_solve_status(s, stream));
+    s->block = best.block;
+    s->run_width = best.run_width;
+    s->lpr = best.lpr;
+    s->sched.nrhs = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_stune_mu);
+        g_stune_cache[key] = best;
+    }
+    if (best_us) *best_us = best.us;
+    return prepare_schedule(s, nrhs);
+}

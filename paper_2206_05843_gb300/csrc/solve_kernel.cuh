@@ -65,6 +65,169 @@ __device__ __forceinline__ T bpart(const SolveArgs<T>& a, int64_t p, int32_t row
     return acc;
 }
 
+// Wide level, several right-hand sides or several lanes per row: the first row of each
+// thread is prepared (coefficients in registers, b-part) before the wait.
+template <typename T>
+__device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ngroups, int grp, int64_t my0,
+                                  int64_t my1, int s) {
+    const int nrhs = a.nrhs;
+    const int64_t pf = my0 + grp;
+    const bool act0 = pf < my1;
+    const bool single = ln.chunks == 1;
+    const int32_t row0 = act0 ? a.perm[pf] : 0;
+    const int f0 = act0 ? a.cptr[pf] : 0, f1 = act0 ? a.cptr[pf + 1] : 0;
+    T pre = T(0);
+    int32_t pcol[PF];
+    T pval[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+        const int q = f0 + ln.el + u * ln.EL;
+        const bool ok = single && q < f1;
+        pcol[u] = ok ? a.ccol[q] : -1;
+        pval[u] = ok ? a.cval[q] : T(0);
+    }
+    if (act0 && single && ln.rl < nrhs) pre = bpart(a, pf, row0, ln.rl, ln);
+    if (!wait_segment(a, s - 1)) return false;
+    for (int64_t base = my0; base < my1; base += ngroups) {
+        const int64_t p = base + grp;
+        const bool act = p < my1;
+        const bool first = base == my0;
+        const int32_t row = act ? (first ? row0 : a.perm[p]) : 0;
+        const int c0 = act ? (first ? f0 : a.cptr[p]) : 0, c1 = act ? (first ? f1 : a.cptr[p + 1]) : 0;
+        for (int j = 0; j < ln.chunks; ++j) {
+            const int k = ln.rl + j * ln.RL;
+            const bool kv = act && k < nrhs;
+            T acc = T(0);
+            if (kv) {
+                int q = c0 + ln.el;
+                if (first && single) {
+                    acc = pre;
+#pragma unroll
+                    for (int u = 0; u < PF; ++u)
+                        if (pcol[u] >= 0) acc -= pval[u] * __ldcg(a.xp + (int64_t)pcol[u] * nrhs + k);
+                    q += PF * ln.EL;
+                } else {
+                    acc = bpart(a, p, row, k, ln);
+                }
+                for (; q < c1; q += ln.EL) acc -= a.cval[q] * __ldcg(a.xp + (int64_t)a.ccol[q] * nrhs + k);
+            }
+            acc = group_reduce(acc, ln);
+            if (kv && ln.el == 0) {
+                __stcg(a.xp + p * nrhs + k, acc);
+                a.x[(int64_t)row + (int64_t)k * a.ld] = acc;
+            }
+        }
+    }
+    return true;
+}
+
+// Wide level, one right-hand side, one lane per row: the first row is prepared before
+// the wait; coefficients come in chunks of four whose gathers are in flight together.
+template <typename T>
+__device__ __forceinline__ T row_1rhs(const SolveArgs<T>& a, int64_t p, int32_t row, int c0, int c1, T acc) {
+    if (a.eptr) {
+        const int e1 = a.eptr[p + 1];
+        for (int q = a.eptr[p]; q < e1; q += 4) {
+            int ec[4];
+            T ev[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = q + u < e1;
+                ec[u] = ok ? a.ecol[q + u] : 0;
+                ev[u] = ok ? a.eval[q + u] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) bv[u] = q + u < e1 ? a.b[ec[u]] : T(0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q + u < e1) acc += ev[u] * bv[u];
+        }
+    }
+    for (int q = c0; q < c1; q += 4) {
+        int cc[4];
+        T cv[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = q + u < c1;
+            cc[u] = ok ? a.ccol[q + u] : 0;
+            cv[u] = ok ? a.cval[q + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = q + u < c1 ? __ldcg(a.xp + cc[u]) : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q + u < c1) acc -= cv[u] * xv[u];
+    }
+    return acc;
+}
+
+template <typename T>
+__device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, int s) {
+    const int64_t pf = my0 + threadIdx.x;
+    const bool act0 = pf < my1;
+    const int32_t row0 = act0 ? a.perm[pf] : 0;
+    const int f0 = act0 ? a.cptr[pf] : 0, f1 = act0 ? a.cptr[pf + 1] : 0;
+    T pre = act0 ? a.dinv[pf] * a.b[row0] : T(0);
+    int32_t pcol[PF];
+    T pval[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+        const bool ok = f0 + u < f1;
+        pcol[u] = ok ? a.ccol[f0 + u] : 0;
+        pval[u] = ok ? a.cval[f0 + u] : T(0);
+    }
+    if (!wait_segment(a, s - 1)) return false;
+    if (act0) {
+        T xv[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) xv[u] = f0 + u < f1 ? __ldcg(a.xp + pcol[u]) : T(0);
+        T acc = pre;
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (f0 + u < f1) acc -= pval[u] * xv[u];
+        acc = row_1rhs(a, pf, row0, f0 + PF < f1 ? f0 + PF : f1, f1, acc);
+        __stcg(a.xp + pf, acc);
+        a.x[row0] = acc;
+    }
+    for (int64_t p = pf + blockDim.x; p < my1; p += blockDim.x) {
+        const int32_t row = a.perm[p];
+        const T acc = row_1rhs(a, p, row, a.cptr[p], a.cptr[p + 1], a.dinv[p] * a.b[row]);
+        __stcg(a.xp + p, acc);
+        a.x[row] = acc;
+    }
+    return true;
+}
+
+// One level per launch (the plain level-set solve): every row of the level is a thread,
+// so the whole level is in flight at full occupancy.  Used when the schedule consists of
+// a few wide levels, where one launch per level costs less than a device-wide handoff
+// would save.
+template <typename T>
+__global__ void __launch_bounds__(256, 8) k_level(SolveArgs<T> a, int64_t p0, int64_t p1) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nrhs = a.nrhs;
+    const int64_t p = p0 + idx / nrhs;
+    const int k = (int)(idx % nrhs);
+    if (p >= p1) return;
+    const int32_t row = a.perm[p];
+    if (nrhs == 1) {
+        const T acc = row_1rhs(a, p, row, a.cptr[p], a.cptr[p + 1], a.dinv[p] * a.b[row]);
+        __stcg(a.xp + p, acc);
+        a.x[row] = acc;
+        return;
+    }
+    T acc = a.dinv[p] * a.b[(int64_t)row + (int64_t)k * a.ld];
+    if (a.eptr)
+        for (int q = a.eptr[p]; q < a.eptr[p + 1]; ++q) acc += a.eval[q] * a.b[(int64_t)a.ecol[q] + (int64_t)k * a.ld];
+    for (int q = a.cptr[p]; q < a.cptr[p + 1]; ++q) acc -= a.cval[q] * __ldcg(a.xp + (int64_t)a.ccol[q] * nrhs + k);
+    __stcg(a.xp + p * nrhs + k, acc);
+    a.x[(int64_t)row + (int64_t)k * a.ld] = acc;
+}
+
+__global__ void k_stamp(unsigned long long* stamps, int64_t l) {
+    if (threadIdx.x == 0) stamps[l] = globaltimer();
+}
+
 // ---------------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------------
@@ -86,95 +249,10 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
             const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
             const int64_t my0 = p0 + (int64_t)me * sg.z;
             const int64_t my1 = min(p1, my0 + (int64_t)sg.z);
-            // everything of the first row that does not depend on x, before the wait
-            const int64_t pf = my0 + grp;
-            const bool act0 = pf < my1;
-            const bool single = ln.chunks == 1;
-            const int32_t row0 = act0 ? a.perm[pf] : 0;
-            const int f0 = act0 ? a.cptr[pf] : 0, f1 = act0 ? a.cptr[pf + 1] : 0;
-            T pre = T(0);
-            int32_t pcol[PF];
-            T pval[PF];
-#pragma unroll
-            for (int u = 0; u < PF; ++u) {
-                const int q = f0 + ln.el + u * ln.EL;
-                const bool ok = single && q < f1;
-                pcol[u] = ok ? a.ccol[q] : -1;
-                pval[u] = ok ? a.cval[q] : T(0);
-            }
-            if (act0 && single && ln.rl < nrhs) pre = bpart(a, pf, row0, ln.rl, ln);
-            if (!wait_segment(a, s - 1)) return;
-            int64_t base = my0;
-            const bool two = nrhs == 1 && a.lpr == 1;
-            for (; base < my1; base += ngroups) {
-                const int64_t p = base + grp;
-                const bool act = p < my1;
-                const bool first = base == my0;
-                if (!first && two) break;  // the rest goes two rows per thread below
-                const int32_t row = act ? (first ? row0 : a.perm[p]) : 0;
-                const int c0 = act ? (first ? f0 : a.cptr[p]) : 0, c1 = act ? (first ? f1 : a.cptr[p + 1]) : 0;
-                for (int j = 0; j < ln.chunks; ++j) {
-                    const int k = ln.rl + j * ln.RL;
-                    const bool kv = act && k < nrhs;
-                    T acc = T(0);
-                    if (kv) {
-                        int q = c0 + ln.el;
-                        if (first && single) {
-                            acc = pre;
-#pragma unroll
-                            for (int u = 0; u < PF; ++u)
-                                if (pcol[u] >= 0) acc -= pval[u] * __ldcg(a.xp + (int64_t)pcol[u] * nrhs + k);
-                            q += PF * ln.EL;
-                        } else {
-                            acc = bpart(a, p, row, k, ln);
-                        }
-                        for (; q < c1; q += ln.EL) acc -= a.cval[q] * __ldcg(a.xp + (int64_t)a.ccol[q] * nrhs + k);
-                    }
-                    acc = group_reduce(acc, ln);
-                    if (kv && ln.el == 0) {
-                        __stcg(a.xp + p * nrhs + k, acc);
-                        a.x[(int64_t)row + (int64_t)k * a.ld] = acc;
-                    }
-                }
-            }
-            // one right-hand side, a row per thread: two independent rows in flight
-            for (; base < my1; base += 2 * ngroups) {
-                const int64_t pa = base + grp, pb = pa + ngroups;
-                const bool aa = pa < my1, ab = pb < my1;
-                const int32_t ra = aa ? a.perm[pa] : 0, rb = ab ? a.perm[pb] : 0;
-                const int ca0 = aa ? a.cptr[pa] : 0, ca1 = aa ? a.cptr[pa + 1] : 0;
-                const int cb0 = ab ? a.cptr[pb] : 0, cb1 = ab ? a.cptr[pb + 1] : 0;
-                T acc_a = aa ? a.dinv[pa] * a.b[ra] : T(0);
-                T acc_b = ab ? a.dinv[pb] * a.b[rb] : T(0);
-                if (a.eptr) {
-                    const int ea0 = aa ? a.eptr[pa] : 0, ea1 = aa ? a.eptr[pa + 1] : 0;
-                    const int eb0 = ab ? a.eptr[pb] : 0, eb1 = ab ? a.eptr[pb + 1] : 0;
-                    for (int q = ea0; q < ea1; ++q) acc_a += a.eval[q] * a.b[a.ecol[q]];
-                    for (int q = eb0; q < eb1; ++q) acc_b += a.eval[q] * a.b[a.ecol[q]];
-                }
-                const int la = ca1 - ca0, lb = cb1 - cb0;
-                const int lmax = la > lb ? la : lb;
-                for (int u = 0; u < lmax; ++u) {
-                    T xa = T(0), xb = T(0), va = T(0), vb = T(0);
-                    if (u < la) {
-                        va = a.cval[ca0 + u];
-                        xa = __ldcg(a.xp + a.ccol[ca0 + u]);
-                    }
-                    if (u < lb) {
-                        vb = a.cval[cb0 + u];
-                        xb = __ldcg(a.xp + a.ccol[cb0 + u]);
-                    }
-                    if (u < la) acc_a -= va * xa;
-                    if (u < lb) acc_b -= vb * xb;
-                }
-                if (aa) {
-                    __stcg(a.xp + pa, acc_a);
-                    a.x[ra] = acc_a;
-                }
-                if (ab) {
-                    __stcg(a.xp + pb, acc_b);
-                    a.x[rb] = acc_b;
-                }
+            if (nrhs == 1 && a.lpr == 1) {
+                if (!wide_rows_1rhs(a, my0, my1, s)) return;
+            } else {
+                if (!wide_rows_general(a, ln, ngroups, grp, my0, my1, s)) return;
             }
             publish(a, s);
             if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());

@@ -295,7 +295,7 @@ sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_wi
         set_error("system_tune: lanes_per_row must be 0 or a power of two <= 32");
         return SPTRSV_ERR_INVALID;
     }
-    if (block < 0 || block > 1024 || run_width < -1) { set_error("system_tune: bad block / run width"); return SPTRSV_ERR_INVALID; }
+    if (block < 0 || block > 1024 || run_width < -2) { set_error("system_tune: bad block / run width"); return SPTRSV_ERR_INVALID; }
     if (block) s->block = block;
     if (run_width) s->run_width = run_width;
     if (lanes_per_row) s->lpr = lanes_per_row;

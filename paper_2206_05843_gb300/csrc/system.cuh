@@ -68,6 +68,7 @@ struct sptrsv_system {
     // solve state
     int block = 512, run_width = 0, lpr = 0;  // 0: automatic
     sp::Schedule sched;
+    std::vector<int32_t> h_cptr;  // host copy of cptr, for cutting run blocks
     sp::DevBuf<int> flags, status;
     sp::DevBuf<unsigned char> xp;
     int withhold = -1;

@@ -136,11 +136,16 @@ def solve_time_us(sysm, bt, reps=5):
     return statistics.median(ts), x
 
 
-def evaluate(pk, mats, cap=1.5, log=None):
+def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
     """Solve time of none / naive / learned; errors against x_true (b = L x_true)."""
     torch = _torch()
     rows = []
+    t0 = time.time()
     for m in mats:
+        if callable(m):
+            if time.time() - t0 > time_budget:
+                break
+            m = m()
         M = B.Matrix.from_host(m)
         lv = B.Levels(M)
         xt, b = S.rhs_from_xtrue(m, 1, 7)
@@ -177,6 +182,7 @@ def main(argv=None):
     ap.add_argument("--out", default="picker_trained.bin")
     ap.add_argument("--report", default="picker_report.json")
     ap.add_argument("--time-budget", type=float, default=1e9, help="seconds for the harvest")
+    ap.add_argument("--eval-budget", type=float, default=1e9, help="seconds for the held-out evaluation")
     a = ap.parse_args(argv)
 
     def log(s):
@@ -206,9 +212,10 @@ def main(argv=None):
     mats = []
     for i in range(a.heldout):
         n = int(round(np.exp(erng.uniform(np.log(a.eval_lo), np.log(a.eval_hi)))))
-        mats.append(S.gen_mixture(n, 20_000 + i))
-    rows, summary = evaluate(pk, mats, log=log)
-    report = {"train_matrices": used, "samples": int(X.shape[0]), "loss_history": hist, "summary": summary,
+        mats.append(lambda n=n, i=i: S.gen_mixture(n, 20_000 + i))
+    rows, summary = evaluate(pk, mats, log=log, time_budget=a.eval_budget)
+    report = {"train_matrices": used, "heldout_requested": a.heldout, "samples": int(X.shape[0]),
+              "loss_history": hist, "summary": summary,
               "heldout": rows, "depths": DEPTHS}
     json.dump(report, open(a.report, "w"), indent=1)
     log(json.dumps(summary))

@@ -416,3 +416,66 @@ def gen_mixture(n: int, seed: int) -> LowerCsr:
     m = gen_from_deps(start, counts, cols, rng, name=f"mixture(n={start},seed={seed})")
     m.meta.update(kind="mixture", seed=seed)
     return m
+
+
+# ----------------------------------------------------------------------------------
+# shapes of the paper's matrices (structure only; the matrices themselves are not
+# available): level counts, level-width profiles and dependency densities as stated
+# in Section IV and Table I
+# ----------------------------------------------------------------------------------
+
+def _from_level_widths(widths, deps_per_row: float, seed: int, window: int = 3, name: str = "") -> LowerCsr:
+    """Rows in level order.  Every row of level l >= 1 takes one dependency in level l-1
+    (so its level is exactly l) and, on average, deps_per_row - 1 more distinct ones
+    uniform over the previous `window` levels."""
+    rng = rng_for(seed)
+    widths = np.asarray(widths, dtype=np.int64)
+    starts = np.concatenate([[0], np.cumsum(widths)])
+    n = int(starts[-1])
+    counts = np.zeros(n, dtype=np.int64)
+    cols = []
+    for l in range(1, widths.size):
+        a, b = int(starts[l]), int(starts[l + 1])
+        lo = int(starts[max(0, l - window)])
+        prev_a, prev_b = int(starts[l - 1]), int(starts[l])
+        for r in range(a, b):
+            d = {int(rng.integers(prev_a, prev_b))}
+            extra = rng.poisson(max(0.0, deps_per_row - 1.0))
+            span = prev_b - lo
+            for _ in range(int(min(extra, span - 1))):
+                d.add(int(rng.integers(lo, prev_b)))
+            s = sorted(d)
+            counts[r] = len(s)
+            cols.extend(s)
+    m = gen_from_deps(n, counts, np.asarray(cols, dtype=np.int64), rng, name=name)
+    m.meta.update(kind=name, seed=seed)
+    return m
+
+
+def gen_lung2_like(seed: int = 0, scale: float = 1.0) -> LowerCsr:
+    """109,460 rows in 479 levels, 453 of them two rows wide (Section IV), the other 26
+    levels wide "bumps"; about 1.5 dependencies per row (Table I's total level cost
+    437,834 = 2 nnz - n gives nnz = 273,647).  ``scale`` narrows the fat levels (same
+    level count) for quick runs."""
+    rng = rng_for(seed + 1)
+    m_levels, n = 479, max(2 * 479, int(109_460 * scale))
+    fat = np.sort(rng.choice(np.arange(1, m_levels), size=26, replace=False))
+    widths = np.full(m_levels, 2, dtype=np.int64)
+    rest = n - 2 * (m_levels - 26)
+    share = rng.dirichlet(np.ones(26)) * rest
+    w = np.floor(share).astype(np.int64)
+    w[: rest - int(w.sum())] += 1
+    widths[fat] = w
+    return _from_level_widths(widths, 1.5, seed, window=2, name="lung2_like")
+
+
+def gen_torso2_like(seed: int = 0, scale: float = 1.0) -> LowerCsr:
+    """115,967 rows in 513 levels with a triangular width profile (Section IV); about
+    3.96 dependencies per row (Table I: 1,035,484 = 2 nnz - n).  ``scale`` narrows the
+    levels (same level count) for quick runs."""
+    m_levels, n = 513, max(2 * 513, int(115_967 * scale))
+    x = np.arange(m_levels)
+    tri = np.minimum(x + 1, m_levels - x).astype(np.float64)
+    widths = np.maximum(1, np.floor(tri / tri.sum() * n)).astype(np.int64)
+    widths[m_levels // 2] += n - int(widths.sum())
+    return _from_level_widths(widths, 3.96, seed, window=3, name="torso2_like")

@@ -158,3 +158,29 @@ def test_bounded_wait_times_out_without_faulting():
     sysm.debug_set_wait(-1, 0)
     x = sysm.solve(bt, check_status=True).cpu().numpy()
     assert rel_l2(x, O.forward_subst(m.rowptr, m.colidx, m.vals, b)) < TOL_F64
+
+
+def test_autotune_keeps_the_solution():
+    torch = torch_cuda()
+    m = S.gen_skewed(40000, 12, head=30000)
+    _, b = S.rhs_from_xtrue(m, 1, 3)
+    M = B.Matrix.from_host(m)
+    lv = B.Levels(M)
+    ref = O.forward_subst(m.rowptr, m.colidx, m.vals, b)
+    for kw in ({}, dict(kind=B.NAIVE, cap=1.5)):
+        s = B.System(M, lv, **kw)
+        us = s.autotune(1)
+        assert us > 0
+        x = s.solve(torch.from_numpy(b).cuda(), check_status=True).cpu().numpy()
+        assert rel_l2(x, ref) <= TOL_F64
+        assert s.autotune(1) == us  # cached by signature
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_per_level_launch_mode(nrhs):
+    """One launch per level (run width -2) gives the same solution."""
+    m = S.gen_layered(6, 30000, 9)
+    b = S.rhs_uniform(m.n, nrhs, 2)
+    solve_and_compare(m, b, TOL_F64, tune=dict(run_width=-2))
+    m2, b2, _ = S.gen_config("c0")
+    solve_and_compare(m2, b2, TOL_F64, system_kw=dict(kind=B.NAIVE, cap=1.5), tune=dict(run_width=-2))
