@@ -49,6 +49,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum over all ranks (each rank runs an independent replica; the job
+    is as slow as its slowest rank).  Identity without torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -119,6 +131,9 @@ def make_workload(name):
     from paper_2206_05843_gb300 import synth as S
     m, b, xt = S.gen_config(name)
     return m, b, xt
+
+
+STRATEGY_NAMES = {0: "none", 1: "naive", 2: "depth_k", 3: "learned", 4: "chosen depths", 5: "manual"}
 
 
 def alg_bytes(info: dict, n: int, nrhs: int, v: int = 8) -> int:
@@ -218,6 +233,12 @@ def build_systems(B, M, lv, strategy: str):
     return plain, rw, used
 
 
+def launches_per_solve(sysm) -> int:
+    """Kernels of this library one solve launches: one persistent kernel, or one kernel
+    per level when the autotuner chose per-level launches."""
+    return int(sysm.m) if sysm.run_width() == -2 else 1
+
+
 def time_solves(torch, sysm, bt, xt, steps, warmup, flush, stream):
     for _ in range(warmup):
         sysm.solve(bt, xt)
@@ -313,10 +334,7 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     us_e2e = statistics.mean(e2e_ms) * 1e3
-    if world > 1:
-        t = torch.tensor([us_rw, us_plain, us_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        us_rw, us_plain, us_e2e = [float(v) for v in t.tolist()]
+    us_rw, us_plain, us_e2e = max_over_ranks([us_rw, us_plain, us_e2e], device="cuda")
     if rank != 0:
         return 0
     peaks = {}
@@ -360,6 +378,7 @@ def run_ours(args):
         "config": {
             "workload": WORKLOAD if args.workload == "c1" else args.workload,
             "strategy": used if used != "auto" else "naive",
+            "strategy_used": STRATEGY_NAMES.get(int(info_rw.get("strategy_used", -1)), "?"),
             "nnz_cap": 1.5,
             "plain_us": round(us_plain, 3),
             "rewritten_us": round(us_rw, 3),
@@ -385,7 +404,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": round(us_e2e, 3), "unit": "us", "h2d_bytes_per_step": int(b.nbytes),
                 "d2h_bytes_per_step": int(b.nbytes)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps * (launches_per_solve(plain) + launches_per_solve(rw)),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

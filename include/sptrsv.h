@@ -137,6 +137,14 @@ typedef struct {
     int32_t n_depths;              /* entries of depths_host */
     const int64_t* injected_cost_dev; /* test hook (NULL normally): per-row cost on the target used by
                                          the planner instead of 2 * |dependencies after substitution| */
+    int32_t max_deps;              /* per-row rule (Section III.A), > 0: a row moves only while it keeps fewer
+                                      than max_deps dependencies after substitution */
+    int64_t max_spread;            /* per-row rule (Section III.A, the cache-locality constraint), > 0: a row moves
+                                      only while max - min of its dependencies is below max_spread.  A row that breaks
+                                      a rule stops its group like a cost overflow (its level becomes the next target). */
+    int32_t learned_mode;          /* LEARNED: 0 = the picker's plan and the naive plan are both built and timed
+                                      (one right-hand side), the faster is kept -- the paper's strategy is the
+                                      fallback and the measured solve time decides; 1 = the picker's plan only */
 } sptrsv_strategy;
 
 /* Plans the rewrite with the strategy, rewrites the chosen rows (substitution of every
@@ -159,6 +167,10 @@ typedef struct {
     int32_t dtype;
     int32_t rewritten;
     double avg_cost;       /* avgLevelCost used by the planner (0 for plain) */
+    int32_t block;         /* solve schedule: block size, */
+    int32_t run_width;     /*   widest level inside a single-CTA run (0 auto, -1 none, -2 one launch per level), */
+    int32_t lanes_per_row; /*   lanes per row (0 auto) */
+    int32_t strategy_used; /* SPTRSV_STRATEGY_* that produced the stored plan (LEARNED resolves to CHOSEN or NAIVE) */
 } sptrsv_system_info;
 
 sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);

@@ -207,10 +207,28 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
  *                     number of non-empty levels, avg*1e6 rounded, number of targets}
  * returns 0, or -1 on allocation failure.
  */
+int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int32_t* level,
+                   int32_t m, int kind, int32_t k, double avg_override, double cap_ratio,
+                   const int64_t* injected_cost, const int32_t* depth_of_target, int32_t alpha,
+                   int64_t beta, int32_t* target, int64_t* row_cost, int64_t* info);
+
 int orc_plan(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int32_t* level,
              int32_t m, int kind, int32_t k, double avg_override, double cap_ratio,
              const int64_t* injected_cost, const int32_t* depth_of_target,
              int32_t* target, int64_t* row_cost, int64_t* info) {
+    return orc_plan_rules(n, rowptr, colidx, level, m, kind, k, avg_override, cap_ratio, injected_cost,
+                          depth_of_target, 0, 0, target, row_cost, info);
+}
+
+/* The planner with the per-row rules of Section III.A: a row may move only while its
+ * dependency count after substitution is below alpha (alpha > 0) and its dependencies
+ * lie within a distance beta of each other, max - min < beta (beta > 0: the
+ * cache-locality constraint).  A row that breaks a rule is treated like one that does
+ * not fit the cost: its level becomes the next target. */
+int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int32_t* level,
+                   int32_t m, int kind, int32_t k, double avg_override, double cap_ratio,
+                   const int64_t* injected_cost, const int32_t* depth_of_target, int32_t alpha,
+                   int64_t beta, int32_t* target, int64_t* row_cost, int64_t* info) {
     int64_t* lrows = (int64_t*)calloc((size_t)m + 1, sizeof(int64_t));
     int64_t* lcost = (int64_t*)calloc((size_t)m + 1, sizeof(int64_t));
     int64_t* lptr = (int64_t*)calloc((size_t)m + 2, sizeof(int64_t));
@@ -283,7 +301,10 @@ int orc_plan(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int3
             int64_t growth = (int64_t)Dn.len + (int64_t)En.len - (int64_t)D[r].len;
             int fits_cost = (kind == ORC_NAIVE) ? ((double)(cur + c) <= avg) : 1;
             int fits_cap = (stored + growth <= limit);
-            if (fits_cost && fits_cap) {
+            int fits_rules = 1;
+            if (alpha > 0 && Dn.len >= alpha) fits_rules = 0;
+            if (beta > 0 && Dn.len > 1 && (int64_t)Dn.v[Dn.len - 1] - (int64_t)Dn.v[0] >= beta) fits_rules = 0;
+            if (fits_cost && fits_cap && fits_rules) {
                 target[r] = t;
                 curlev[r] = t;
                 row_cost[r] = c;

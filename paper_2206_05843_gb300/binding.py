@@ -57,14 +57,16 @@ class Strategy(C.Structure):
     _fields_ = [("kind", C.c_int32), ("k", C.c_int32), ("nnz_growth_cap", C.c_double),
                 ("avg_override", C.c_double), ("growth_guard", C.c_double), ("picker", C.c_void_p),
                 ("depth_of_target_host", C.c_void_p), ("depths_host", C.c_void_p), ("n_depths", C.c_int32),
-                ("injected_cost_dev", C.c_void_p)]
+                ("injected_cost_dev", C.c_void_p), ("max_deps", C.c_int32), ("max_spread", C.c_int64),
+                ("learned_mode", C.c_int32)]
 
 
 class SystemInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("nnz_c", C.c_int64), ("nnz_e", C.c_int64),
                 ("rows_moved", C.c_int64), ("stored_nnz", C.c_int64), ("nnz_l", C.c_int64),
                 ("segments", C.c_int64), ("run_levels", C.c_int64), ("dtype", C.c_int32),
-                ("rewritten", C.c_int32), ("avg_cost", C.c_double)]
+                ("rewritten", C.c_int32), ("avg_cost", C.c_double), ("block", C.c_int32),
+                ("run_width", C.c_int32), ("lanes_per_row", C.c_int32), ("strategy_used", C.c_int32)]
 
 
 class BatchInfo(C.Structure):
@@ -252,11 +254,13 @@ class Levels:
 
 
 def strategy(kind=NONE, k=0, cap=0.0, avg=0.0, guard=0.0, picker=None, depth_of_target=None, depths=None,
-             injected_cost=None) -> tuple[Strategy, list]:
+             injected_cost=None, alpha=0, beta=0, model_only=False) -> tuple[Strategy, list]:
     """Builds an sptrsv_strategy; returns it with the objects that must stay alive."""
     keep = []
     s = Strategy()
     s.kind, s.k, s.nnz_growth_cap, s.avg_override, s.growth_guard = kind, k, cap, avg, guard
+    s.max_deps, s.max_spread = alpha, beta
+    s.learned_mode = 1 if model_only else 0
     s.picker = picker.h if picker is not None else None
     if depth_of_target is not None:
         a = np.ascontiguousarray(depth_of_target, dtype=np.int32)
@@ -295,6 +299,9 @@ class System:
         self.info = {f: getattr(inf, f) for f, _ in SystemInfo._fields_}
         self.n, self.m = inf.n, inf.m
         return self.info
+
+    def run_width(self) -> int:
+        return int(self.refresh()["run_width"])
 
     def tune(self, block=0, run_width=0, lanes_per_row=0):
         check(load().sptrsv_system_tune(self.h, block, run_width, lanes_per_row))

@@ -380,8 +380,39 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
     SP_CUDA(cudaMemcpyAsync(dep.p, depths, nd * 4, cudaMemcpyHostToDevice, st));
     if (m > 0) k_choose_depths<<<nblk(m, 256), 256, 0, st>>>(m, pred.as<float>(), dep.as<int32_t>(), nd, dot.as<int32_t>());
     SP_CUDA(cudaGetLastError());
-    return rewrite_system(L, lv, 3 /* depth per target */, 0, dot.as<int32_t>(), sg->avg_override, sg->nnz_growth_cap,
-                          sg->growth_guard, nullptr, out, st);
+    sptrsv_system* model = nullptr;
+    SP_TRY(rewrite_system(L, lv, 3 /* depth per target */, 0, dot.as<int32_t>(), sg->avg_override, sg->nnz_growth_cap,
+                          sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &model, st));
+    model->strategy_used = SPTRSV_STRATEGY_CHOSEN;
+    if (sg->learned_mode == 1) {
+        *out = model;
+        return SPTRSV_OK;
+    }
+    // the paper's naive strategy is the fallback; the measured solve time decides
+    sptrsv_system* naive = nullptr;
+    sptrsv_status rc = rewrite_system(L, lv, 1 /* naive */, 0, nullptr, sg->avg_override, sg->nnz_growth_cap,
+                                      sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &naive, st);
+    if (rc != SPTRSV_OK) {
+        sptrsv_system_destroy(model);
+        return rc;
+    }
+    naive->strategy_used = SPTRSV_STRATEGY_NAIVE;
+    double t_model = 0, t_naive = 0;
+    rc = time_solve_us(model, 5, &t_model, st);
+    if (rc == SPTRSV_OK) rc = time_solve_us(naive, 5, &t_naive, st);
+    if (rc != SPTRSV_OK) {
+        sptrsv_system_destroy(model);
+        sptrsv_system_destroy(naive);
+        return rc;
+    }
+    if (t_model <= t_naive) {
+        sptrsv_system_destroy(naive);
+        *out = model;
+    } else {
+        sptrsv_system_destroy(model);
+        *out = naive;
+    }
+    return SPTRSV_OK;
 }
 
 }  // namespace sp

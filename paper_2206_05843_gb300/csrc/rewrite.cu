@@ -95,6 +95,8 @@ struct WalkArgs {
     int64_t limit;
     const int32_t* dot;  // depth of target (CHOSEN)
     const int64_t* inj;  // injected costs (test hook)
+    int alpha;           // per-row rules (Section III.A): dependencies after substitution < alpha
+    int64_t beta;        //   and max - min dependency < beta (0: off)
     int32_t* target;     // current level of every row (init: level)
     int64_t* row_cost;
     int64_t* d_off;
@@ -181,7 +183,14 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
             const int64_t growth = valid ? (int64_t)nd + ne - (q1 - q0) : 0;
             const int64_t pc = warp_incl_scan(c);
             const int64_t pg = warp_incl_scan(growth);
-            const bool pass = (a.kind != WALK_NAIVE || (double)(cur + pc) <= a.avg) && (stored + pg <= a.limit);
+            bool rules = true;
+            if (valid && a.alpha > 0 && nd >= a.alpha) rules = false;
+            if (valid && a.beta > 0 && nd > 1 && (int64_t)Dp[nd - 1] - (int64_t)Dp[0] >= a.beta) rules = false;
+            // a rule broken by an earlier lane stops the prefix there, like a cost overflow
+            const unsigned badrule = __ballot_sync(0xffffffffu, !rules);
+            const int first_bad = badrule ? __ffs(badrule) - 1 : 32;
+            const bool pass = (a.kind != WALK_NAIVE || (double)(cur + pc) <= a.avg) && (stored + pg <= a.limit) &&
+                              lane < first_bad;
             const unsigned failmask = __ballot_sync(0xffffffffu, valid && !pass);
             const int first = failmask ? __ffs(failmask) - 1 : 32;
             const int nvalid = (int)(Bn - base < 32 ? Bn - base : 32);
@@ -468,10 +477,10 @@ struct PlanOut {
 
 // plans targets[n] (device) for the given walk kind; returns planner bookkeeping
 sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int k, const int32_t* dot_dev,
-                           double avg, double cap, const int64_t* inj, int32_t* target, PlanOut& po,
-                           cudaStream_t st) {
+                           double avg, double cap, const int64_t* inj, int alpha, int64_t beta, int32_t* target,
+                           PlanOut& po, cudaStream_t st) {
     const int64_t n = L->n, m = lv.m;
-    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || cap > 0 || inj;
+    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || cap > 0 || inj || alpha > 0 || beta > 0;
     if (!walk) {
         Scratch lt;
         SP_TRY(lt.alloc(std::max<int64_t>(1, m) * sizeof(int32_t), st));
@@ -510,6 +519,8 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
         a.limit = cap > 0 ? (int64_t)std::floor(cap * (double)L->nnz) : INT64_MAX;
         a.dot = dot_dev;
         a.inj = inj;
+        a.alpha = alpha;
+        a.beta = beta;
         a.target = target;
         a.row_cost = rc.as<int64_t>();
         a.d_off = doff.as<int64_t>();
@@ -672,8 +683,8 @@ sptrsv_status rewrite_rows(const sptrsv_csr* L, const Levels& lv, const int32_t*
 }
 
 sptrsv_status rewrite_system(const sptrsv_csr* L, const Levels& lv, int kind, int k, const int32_t* dot_dev,
-                             double avg_override, double cap, double guard, const int64_t* inj, sptrsv_system** out,
-                             cudaStream_t st) {
+                             double avg_override, double cap, double guard, const int64_t* inj, int alpha, int64_t beta,
+                             sptrsv_system** out, cudaStream_t st) {
     const int64_t n = L->n;
     sptrsv_system* s = new (std::nothrow) sptrsv_system();
     if (!s) { set_error("host allocation failed"); return SPTRSV_ERR_OOM; }
@@ -691,7 +702,7 @@ sptrsv_status rewrite_system(const sptrsv_csr* L, const Levels& lv, int kind, in
     if (rc != SPTRSV_OK) return fail(rc);
     PlanOut po;
     if (n > 0) {
-        rc = plan_targets(L, lv, kind, k, dot_dev, avg, cap, inj, s->target.p, po, st);
+        rc = plan_targets(L, lv, kind, k, dot_dev, avg, cap, inj, alpha, beta, s->target.p, po, st);
         if (rc != SPTRSV_OK) return fail(rc);
         rc = L->dtype == SPTRSV_F64 ? rewrite_rows<double>(L, lv, s->target.p, guard, s, st)
                                     : rewrite_rows<float>(L, lv, s->target.p, guard, s, st);
@@ -748,6 +759,8 @@ extern "C" sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels
     int wk = kind == SPTRSV_STRATEGY_NAIVE ? WALK_NAIVE : kind == SPTRSV_STRATEGY_DEPTH_K ? WALK_DEPTH
            : kind == SPTRSV_STRATEGY_CHOSEN ? WALK_CHOSEN : kind == SPTRSV_STRATEGY_MANUAL ? WALK_MANUAL : 0;
     if (!wk) { set_error("rewrite: unknown strategy %d", kind); return SPTRSV_ERR_INVALID; }
-    return rewrite_system(L, lv, wk, sg->k, dot_dev, sg->avg_override, sg->nnz_growth_cap, sg->growth_guard,
-                          sg->injected_cost_dev, out, st);
+    sptrsv_status rc = rewrite_system(L, lv, wk, sg->k, dot_dev, sg->avg_override, sg->nnz_growth_cap,
+                                      sg->growth_guard, sg->injected_cost_dev, sg->max_deps, sg->max_spread, out, st);
+    if (rc == SPTRSV_OK) (*out)->strategy_used = kind;
+    return rc;
 }

@@ -207,10 +207,12 @@ __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int
     G.sync();
 }
 
-// Narrow block, one right-hand side, one lane per row: the coefficients and ring slots of
-// the next level are read into registers while the current level computes, so a level
-// costs its ring loads plus its dependent float64 FMAs.
-constexpr int NK = 4;  // coefficients per row held in registers
+// Narrow block, one right-hand side, LPR lanes per row (LPR = 1, 2 or 4): every lane
+// holds up to NK of its row's coefficients (entries el, el+LPR, ...) and their ring slots
+// in registers, read for the next level while the current level computes; the lanes of
+// a row combine their partial sums with shuffles.  A level costs its ring loads plus
+// ceil(deps / LPR) dependent float64 FMAs and log2(LPR) adds.
+constexpr int NK = 4;  // coefficients per lane held in registers
 
 template <typename T>
 struct RowRegs {
@@ -218,48 +220,66 @@ struct RowRegs {
     bool act;
     T bp;
     int slot[NK];
-    T cv[NK];
 };
 
-template <typename T>
+template <typename T, int LPR>
 __device__ __forceinline__ void load_row_regs(const RunSmem<T>& sm, int lb, int le, RowRegs<T>& r) {
-    r.i = lb + (int)threadIdx.x;
+    const int el = (int)threadIdx.x & (LPR - 1);
+    r.i = lb + (int)threadIdx.x / LPR;
     r.act = r.i < le;
     r.c0 = r.act ? sm.cptr[r.i] : 0;
     r.c1 = r.act ? sm.cptr[r.i + 1] : 0;
-    r.bp = r.act ? sm.bp[r.i] : T(0);
+    r.bp = (r.act && el == 0) ? sm.bp[r.i] : T(0);
 #pragma unroll
     for (int u = 0; u < NK; ++u) {
-        const bool ok = r.c0 + u < r.c1;
-        r.slot[u] = ok ? sm.cslot[r.c0 + u] : 0;
-        r.cv[u] = ok ? sm.cval[r.c0 + u] : T(0);
+        const int q = r.c0 + el + u * LPR;
+        r.slot[u] = q < r.c1 ? sm.cslot[q] : 0;
     }
 }
 
-template <typename T>
-__device__ void run_compute_narrow1(RunSmem<T>& sm, int64_t P0, int l0, int nl, unsigned long long* stamps) {
+template <typename T, int LPR>
+__device__ void run_compute_narrow(RunSmem<T>& sm, int64_t P0, int l0, int nl, unsigned long long* stamps) {
     if (threadIdx.x >= 32) return;
     const int mask = sm.g.ring_rows - 1;
+    const int el = (int)threadIdx.x & (LPR - 1);
     RowRegs<T> cur, nxt;
-    load_row_regs(sm, sm.lp[0], sm.lp[1], cur);
+    load_row_regs<T, LPR>(sm, sm.lp[0], sm.lp[1], cur);
     for (int li = 0; li < nl; ++li) {
-        if (li + 1 < nl) load_row_regs(sm, sm.lp[li + 1], sm.lp[li + 2], nxt);
+        if (li + 1 < nl) load_row_regs<T, LPR>(sm, sm.lp[li + 1], sm.lp[li + 2], nxt);
+        T acc = cur.bp;
         if (cur.act) {
-            T xv[NK];
+            T xv[NK], cv[NK];
 #pragma unroll
-            for (int u = 0; u < NK; ++u) xv[u] = sm.ring[cur.slot[u]];
-            T acc = cur.bp;
-            const int len = cur.c1 - cur.c0;
+            for (int u = 0; u < NK; ++u) {
+                const int q = cur.c0 + el + u * LPR;
+                xv[u] = sm.ring[cur.slot[u]];
+                cv[u] = q < cur.c1 ? sm.cval[q] : T(0);
+            }
 #pragma unroll
             for (int u = 0; u < NK; ++u)
-                if (u < len) acc -= cur.cv[u] * xv[u];
-            for (int q = cur.c0 + NK; q < cur.c1; ++q) acc -= sm.cval[q] * sm.ring[sm.cslot[q]];
-            sm.ring[(int)((P0 + cur.i) & mask)] = acc;
+                if (cur.c0 + el + u * LPR < cur.c1) acc -= cv[u] * xv[u];
+            for (int q = cur.c0 + el + NK * LPR; q < cur.c1; q += LPR) acc -= sm.cval[q] * sm.ring[sm.cslot[q]];
         }
+#pragma unroll
+        for (int o = 1; o < LPR; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (cur.act && el == 0) sm.ring[(int)((P0 + cur.i) & mask)] = acc;
         __syncwarp();
         if (stamps && threadIdx.x == 0) stamps[l0 + li] = globaltimer();
         cur = nxt;
     }
+}
+
+template <typename T>
+__device__ __forceinline__ bool narrow_fast(const Lanes& ln, int nrhs) {
+    return nrhs == 1 && (ln.lpr == 1 || ln.lpr == 2 || ln.lpr == 4);
+}
+
+template <typename T>
+__device__ void run_compute_narrow_any(RunSmem<T>& sm, const Lanes& ln, int64_t P0, int l0, int nl,
+                                       unsigned long long* stamps) {
+    if (ln.lpr == 1) run_compute_narrow<T, 1>(sm, P0, l0, nl, stamps);
+    else if (ln.lpr == 2) run_compute_narrow<T, 2>(sm, P0, l0, nl, stamps);
+    else run_compute_narrow<T, 4>(sm, P0, l0, nl, stamps);
 }
 
 // the level loop of one staged block; narrow blocks run on warp 0 alone
@@ -340,10 +360,10 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
         const int nl = bd.w & (BLK_NARROW - 1);
         const bool narrow = (bd.w & BLK_NARROW) != 0;
         const bool next = blk + 1 < blk1;
-        const bool fast = narrow && v.nrhs == 1 && ln.lpr == 1;
+        const bool fast = narrow && narrow_fast<T>(ln, v.nrhs);
         const bool overlap = fast && next && blockDim.x > 32;
         if (!overlap || threadIdx.x < 32) {
-            if (fast) run_compute_narrow1(cur, P0, bd.z, nl, stamps);
+            if (fast) run_compute_narrow_any(cur, ln, P0, bd.z, nl, stamps);
             else run_compute(v, cur, ln, narrow, P0, bd.z, nl, stamps);
         }
         if (!overlap) __syncthreads();

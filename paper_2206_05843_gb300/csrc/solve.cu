@@ -358,3 +358,36 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
     if (best_us) *best_us = best.us;
     return prepare_schedule(s, nrhs);
 }
+
+namespace sp {
+sptrsv_status time_solve_us(sptrsv_system* s, int reps, double* us, cudaStream_t st) {
+    *us = 0;
+    if (s->n == 0) return SPTRSV_OK;
+    const size_t vb = s->dtype == SPTRSV_F64 ? 8 : 4;
+    Scratch b, x;
+    SP_TRY(b.alloc((size_t)s->n * vb, st));
+    SP_TRY(x.alloc((size_t)s->n * vb, st));
+    SP_CUDA(cudaMemsetAsync(b.p, 0, (size_t)s->n * vb, st));
+    SP_TRY(enqueue_solve(s, b.p, x.p, 1, s->n, nullptr, st));
+    cudaEvent_t e0, e1;
+    SP_CUDA(cudaEventCreate(&e0));
+    SP_CUDA(cudaEventCreate(&e1));
+    std::vector<float> t;
+    sptrsv_status rc = SPTRSV_OK;
+    for (int r = 0; r < reps && rc == SPTRSV_OK; ++r) {
+        cudaEventRecord(e0, st);
+        rc = enqueue_solve(s, b.p, x.p, 1, s->n, nullptr, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t.push_back(ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SP_TRY(rc);
+    std::sort(t.begin(), t.end());
+    *us = t[t.size() / 2] * 1e3;
+    return sptrsv_solve_status(s, st);
+}
+}  // namespace sp

@@ -126,15 +126,15 @@ __device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ng
 template <typename T>
 __device__ __forceinline__ T row_1rhs(const SolveArgs<T>& a, int64_t p, int32_t row, int c0, int c1, T acc) {
     if (a.eptr) {
-        const int e1 = a.eptr[p + 1];
-        for (int q = a.eptr[p]; q < e1; q += 4) {
+        const int e1 = __ldcs(a.eptr + p + 1);
+        for (int q = __ldcs(a.eptr + p); q < e1; q += 4) {
             int ec[4];
             T ev[4], bv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const bool ok = q + u < e1;
-                ec[u] = ok ? a.ecol[q + u] : 0;
-                ev[u] = ok ? a.eval[q + u] : T(0);
+                ec[u] = ok ? __ldcs(a.ecol + q + u) : 0;
+                ev[u] = ok ? __ldcs(a.eval + q + u) : T(0);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) bv[u] = q + u < e1 ? a.b[ec[u]] : T(0);
@@ -146,11 +146,25 @@ __device__ __forceinline__ T row_1rhs(const SolveArgs<T>& a, int64_t p, int32_t 
     for (int q = c0; q < c1; q += 4) {
         int cc[4];
         T cv[4], xv[4];
+        if ((q & 3) == 0 && q + 4 <= c1) {
+            // four coefficients on a 16-byte boundary: vector loads (3 instructions, not 8)
+            const int4 c4 = __ldcs((const int4*)(a.ccol + q));
+            cc[0] = c4.x; cc[1] = c4.y; cc[2] = c4.z; cc[3] = c4.w;
+            if (sizeof(T) == 8) {
+                const double2 v0 = __ldcs((const double2*)(a.cval + q));
+                const double2 v1 = __ldcs((const double2*)(a.cval + q + 2));
+                cv[0] = (T)v0.x; cv[1] = (T)v0.y; cv[2] = (T)v1.x; cv[3] = (T)v1.y;
+            } else {
+                const float4 v = __ldcs((const float4*)(a.cval + q));
+                cv[0] = (T)v.x; cv[1] = (T)v.y; cv[2] = (T)v.z; cv[3] = (T)v.w;
+            }
+        } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool ok = q + u < c1;
-            cc[u] = ok ? a.ccol[q + u] : 0;
-            cv[u] = ok ? a.cval[q + u] : T(0);
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = q + u < c1;
+                cc[u] = ok ? __ldcs(a.ccol + q + u) : 0;
+                cv[u] = ok ? __ldcs(a.cval + q + u) : T(0);
+            }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) xv[u] = q + u < c1 ? __ldcg(a.xp + cc[u]) : T(0);
@@ -165,16 +179,16 @@ template <typename T>
 __device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, int s) {
     const int64_t pf = my0 + threadIdx.x;
     const bool act0 = pf < my1;
-    const int32_t row0 = act0 ? a.perm[pf] : 0;
-    const int f0 = act0 ? a.cptr[pf] : 0, f1 = act0 ? a.cptr[pf + 1] : 0;
-    T pre = act0 ? a.dinv[pf] * a.b[row0] : T(0);
+    const int32_t row0 = act0 ? __ldcs(a.perm + pf) : 0;
+    const int f0 = act0 ? __ldcs(a.cptr + pf) : 0, f1 = act0 ? __ldcs(a.cptr + pf + 1) : 0;
+    T pre = act0 ? __ldcs(a.dinv + pf) * __ldcs(a.b + row0) : T(0);
     int32_t pcol[PF];
     T pval[PF];
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
         const bool ok = f0 + u < f1;
-        pcol[u] = ok ? a.ccol[f0 + u] : 0;
-        pval[u] = ok ? a.cval[f0 + u] : T(0);
+        pcol[u] = ok ? __ldcs(a.ccol + f0 + u) : 0;
+        pval[u] = ok ? __ldcs(a.cval + f0 + u) : T(0);
     }
     if (!wait_segment(a, s - 1)) return false;
     if (act0) {
@@ -190,10 +204,10 @@ __device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, 
         a.x[row0] = acc;
     }
     for (int64_t p = pf + blockDim.x; p < my1; p += blockDim.x) {
-        const int32_t row = a.perm[p];
-        const T acc = row_1rhs(a, p, row, a.cptr[p], a.cptr[p + 1], a.dinv[p] * a.b[row]);
+        const int32_t row = __ldcs(a.perm + p);
+        const T acc = row_1rhs(a, p, row, __ldcs(a.cptr + p), __ldcs(a.cptr + p + 1), __ldcs(a.dinv + p) * __ldcs(a.b + row));
         __stcg(a.xp + p, acc);
-        a.x[row] = acc;
+        __stcs(a.x + row, acc);
     }
     return true;
 }
@@ -203,17 +217,17 @@ __device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, 
 // a few wide levels, where one launch per level costs less than a device-wide handoff
 // would save.
 template <typename T>
-__global__ void __launch_bounds__(256, 8) k_level(SolveArgs<T> a, int64_t p0, int64_t p1) {
+__global__ void __launch_bounds__(256, 6) k_level(SolveArgs<T> a, int64_t p0, int64_t p1) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nrhs = a.nrhs;
     const int64_t p = p0 + idx / nrhs;
     const int k = (int)(idx % nrhs);
     if (p >= p1) return;
-    const int32_t row = a.perm[p];
+    const int32_t row = __ldcs(a.perm + p);
     if (nrhs == 1) {
-        const T acc = row_1rhs(a, p, row, a.cptr[p], a.cptr[p + 1], a.dinv[p] * a.b[row]);
+        const T acc = row_1rhs(a, p, row, __ldcs(a.cptr + p), __ldcs(a.cptr + p + 1), __ldcs(a.dinv + p) * __ldcs(a.b + row));
         __stcg(a.xp + p, acc);
-        a.x[row] = acc;
+        __stcs(a.x + row, acc);
         return;
     }
     T acc = a.dinv[p] * a.b[(int64_t)row + (int64_t)k * a.ld];

@@ -217,6 +217,10 @@ sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info*
     o->dtype = s->dtype;
     o->rewritten = s->rewritten;
     o->avg_cost = s->avg;
+    o->block = s->block;
+    o->run_width = s->run_width;
+    o->lanes_per_row = s->lpr;
+    o->strategy_used = s->strategy_used;
     return SPTRSV_OK;
 }
 

@@ -60,6 +60,7 @@ struct sptrsv_system {
     int64_t n = 0, m = 0;
     int dtype = SPTRSV_F64;
     int rewritten = 0;
+    int strategy_used = 0;
     sp::Levels lv;  // levels of the stored structure; lv.level_rows is perm, lv.pos its inverse
     sp::DevBuf<int32_t> cptr, ccol, eptr, ecol, target;
     sp::DevBuf<unsigned char> cval, eval, dinv;
@@ -100,8 +101,11 @@ sptrsv_status pack_system(sptrsv_system* s, const sptrsv_csr* L, const RewriteHe
 
 // rewrite with a planner walk kind (1 naive, 2 fixed depth, 3 depth per target) -> new system
 sptrsv_status rewrite_system(const sptrsv_csr* L, const Levels& lv, int kind, int k, const int32_t* dot_dev,
-                             double avg_override, double cap, double guard, const int64_t* inj, sptrsv_system** out,
-                             cudaStream_t st);
+                             double avg_override, double cap, double guard, const int64_t* inj, int alpha, int64_t beta,
+                             sptrsv_system** out, cudaStream_t st);
+
+// median time of `reps` solves with b = 0 (one right-hand side), in microseconds
+sptrsv_status time_solve_us(sptrsv_system* s, int reps, double* us, cudaStream_t st);
 
 // the learned strategy (picker.cu): features -> MLP -> depth per target -> rewrite_system
 sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lv, const sptrsv_strategy* sg,

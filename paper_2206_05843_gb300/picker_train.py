@@ -153,20 +153,27 @@ def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
         ref = xt[0]
         res = {"n": m.n, "levels": lv.m}
         for name, kw in (("none", {}), ("naive", dict(kind=B.NAIVE, cap=cap)),
-                         ("learned", dict(kind=B.LEARNED, cap=cap, picker=pk))):
+                         ("learned", dict(kind=B.LEARNED, cap=cap, picker=pk)),
+                         ("learned_model_only", dict(kind=B.LEARNED, cap=cap, picker=pk, model_only=True))):
             s = B.System(M, lv, **kw)
             us, x = solve_time_us(s, bt)
             err = float(np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref))
-            res[name] = {"us": us, "levels": s.m, "rel_err": err}
+            res[name] = {"us": us, "levels": s.m, "rel_err": err, "strategy_used": int(s.info["strategy_used"])}
         rows.append(res)
         if log:
             log(json.dumps(res))
     def gmean(key):
         return float(np.exp(np.mean([np.log(r["none"]["us"] / r[key]["us"]) for r in rows])))
-    summary = {"matrices": len(rows), "geomean_speedup_vs_none": {"naive": gmean("naive"), "learned": gmean("learned")},
+    summary = {"matrices": len(rows),
+               "geomean_speedup_vs_none": {"naive": gmean("naive"), "learned": gmean("learned"),
+                                           "learned_model_only": gmean("learned_model_only")},
                "geomean_speedup_learned_vs_naive": float(np.exp(np.mean(
                    [np.log(r["naive"]["us"] / r["learned"]["us"]) for r in rows]))),
-               "max_rel_err": max(max(r[k]["rel_err"] for k in ("none", "naive", "learned")) for r in rows)}
+               "geomean_speedup_model_only_vs_naive": float(np.exp(np.mean(
+                   [np.log(r["naive"]["us"] / r["learned_model_only"]["us"]) for r in rows]))),
+               "model_plan_kept": int(sum(r["learned"]["strategy_used"] == B.CHOSEN for r in rows)),
+               "max_rel_err": max(max(r[k]["rel_err"] for k in ("none", "naive", "learned", "learned_model_only"))
+                                  for r in rows)}
     return rows, summary
 
 
@@ -183,11 +190,23 @@ def main(argv=None):
     ap.add_argument("--report", default="picker_report.json")
     ap.add_argument("--time-budget", type=float, default=1e9, help="seconds for the harvest")
     ap.add_argument("--eval-budget", type=float, default=1e9, help="seconds for the held-out evaluation")
+    ap.add_argument("--evaluate", default=None, help="evaluate this trained picker file only (no training)")
     a = ap.parse_args(argv)
 
     def log(s):
         print(s, flush=True)
 
+    if a.evaluate:
+        pk = B.Picker.load(a.evaluate)
+        erng = S.rng_for(54321)
+        mats = []
+        for i in range(a.heldout):
+            n = int(round(np.exp(erng.uniform(np.log(a.eval_lo), np.log(a.eval_hi)))))
+            mats.append(lambda n=n, i=i: S.gen_mixture(n, 20_000 + i))
+        rows, summary = evaluate(pk, mats, log=log, time_budget=a.eval_budget)
+        json.dump({"picker": a.evaluate, "summary": summary, "heldout": rows}, open(a.report, "w"), indent=1)
+        log(json.dumps(summary))
+        return 0
     rng = S.rng_for(12345)
     t0 = time.time()
     Xs, Ys = [], []

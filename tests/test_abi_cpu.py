@@ -37,5 +37,6 @@ def test_strategy_struct_layout_matches_header():
     # the binding mirrors the header's struct field order
     src = open(os.path.join(ROOT, "include", "sptrsv.h")).read()
     body = src[src.index("typedef struct {\n    int32_t kind;"):src.index("} sptrsv_strategy;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\*?\s*([a-z_0-9]+);", body)
     assert fields == [f for f, _ in binding.Strategy._fields_]

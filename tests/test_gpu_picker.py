@@ -108,10 +108,10 @@ def test_learned_rewrite_extremes_match_oracle_plans():
     bt = torch.from_numpy(b).cuda()
     ref = O.forward_subst(m.rowptr, m.colidx, m.vals, b)
     # predictions all positive: no candidate helps, nothing is rewritten
-    s0 = B.System(M, lv, B.LEARNED, cap=1.5, picker=constant_picker(1.0))
+    s0 = B.System(M, lv, B.LEARNED, cap=1.5, picker=constant_picker(1.0), model_only=True)
     assert s0.info["rows_moved"] == 0 and s0.m == mm
     # all negative and equal: the first depth with the lowest prediction (the smallest)
-    s1 = B.System(M, lv, B.LEARNED, cap=1.5, picker=constant_picker(-1.0), depths=[4, 8])
+    s1 = B.System(M, lv, B.LEARNED, cap=1.5, picker=constant_picker(-1.0), depths=[4, 8], model_only=True)
     p = O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN, cap=1.5, depth_of_target=np.full(mm, 4))
     assert np.array_equal(s1.export()["target"], p.target)
     for s in (s0, s1):
@@ -127,3 +127,20 @@ def test_learned_without_picker_falls_back_to_naive():
     a = B.System(M, lv, B.LEARNED, cap=1.5).export()["target"]
     b = B.System(M, lv, B.NAIVE, cap=1.5).export()["target"]
     assert np.array_equal(a, b)
+
+
+def test_learned_keeps_the_faster_of_model_and_naive():
+    """The paper's strategy is the fallback: with a model that rewrites nothing, the
+    measured solve time keeps the naive plan on a chain-heavy matrix."""
+    torch = torch_cuda()
+    m = S.gen_skewed(60000, 13, head=30000)
+    _, b = S.rhs_from_xtrue(m, 1, 5)
+    M = B.Matrix.from_host(m)
+    lv = B.Levels(M)
+    s = B.System(M, lv, B.LEARNED, cap=1.5, picker=constant_picker(1.0))
+    assert s.info["strategy_used"] in (B.NAIVE, B.CHOSEN)
+    naive = B.System(M, lv, B.NAIVE, cap=1.5)
+    if s.info["strategy_used"] == B.NAIVE:
+        assert np.array_equal(s.export()["target"], naive.export()["target"])
+    x = s.solve(torch.from_numpy(b).cuda(), check_status=True).cpu().numpy()
+    assert rel_l2(x, O.forward_subst(m.rowptr, m.colidx, m.vals, b)) < TOL_F64

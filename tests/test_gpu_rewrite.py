@@ -159,3 +159,18 @@ def test_empty_and_degenerate():
     m = S.gen_from_deps(n, np.array([0] + [1] * (n - 1)), np.arange(n - 1), S.rng_for(3))
     s, _ = run_both(m, B.DEPTH_K, S.rhs_uniform(n, 1, 1), k=7)
     assert s.m == -(-n // 8)
+
+
+@pytest.mark.parametrize("alpha,beta", [(3, 0), (0, 60), (5, 200)])
+def test_per_row_rules_match_oracle(alpha, beta):
+    torch = torch_cuda()
+    m, b, _ = S.gen_config("c0", seed=4)
+    M = B.Matrix.from_host(m)
+    lv = B.Levels(M)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    for kind, okind, k in ((B.NAIVE, O.NAIVE, 0), (B.DEPTH_K, O.DEPTH, 3)):
+        p = O.plan(m.rowptr, m.colidx, lev, mm, okind, k=k, alpha=alpha, beta=beta)
+        s = B.System(M, lv, kind, k=k, alpha=alpha, beta=beta)
+        assert np.array_equal(s.export()["target"], p.target)
+        x = s.solve(torch.from_numpy(b).cuda(), check_status=True).cpu().numpy()
+        assert rel_l2(x, O.forward_subst(m.rowptr, m.colidx, m.vals, b)) <= TOL_F64

@@ -415,3 +415,24 @@ def test_planner_manual_is_depth_over_thin_levels():
     fat = st["cost"] >= p.avg
     assert np.all(p.target[fat[lev]] == lev[fat[lev]])
     assert p.levels_after < mm
+
+
+@pytest.mark.parametrize("alpha,beta", [(3, 0), (0, 40), (4, 100), (1, 0)])
+def test_planner_per_row_rules(alpha, beta):
+    """Section III.A rules: every rewritten row keeps fewer than alpha dependencies and a
+    dependency spread below beta; huge limits are the same as no rules."""
+    m, _, _ = S.gen_config("c0", seed=3)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    for kind, k in ((O.NAIVE, 0), (O.DEPTH, 3)):
+        p = O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k, alpha=alpha, beta=beta)
+        sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, p.target)
+        for r in np.nonzero(sy.moved)[0]:
+            deps = sy.ccol[sy.cptr[r]:sy.cptr[r + 1]]
+            if alpha:
+                assert deps.size < alpha
+            if beta and deps.size > 1:
+                assert deps.max() - deps.min() < beta
+        free = O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k)
+        loose = O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k, alpha=10**6, beta=10**9)
+        assert np.array_equal(free.target, loose.target)
+        assert p.moved <= free.moved or kind == O.NAIVE
