@@ -239,7 +239,9 @@ def launches_per_solve(sysm) -> int:
     return int(sysm.m) if sysm.run_width() == -2 else 1
 
 
-def time_solves(torch, sysm, bt, xt, steps, warmup, flush, stream):
+def time_solves(torch, sysm, bt, xt, steps, warmup, flush, stream, label):
+    """Times `steps` solves; the timed solves sit in the NVTX range `label`, so that a profiler
+    can capture exactly them (ncu --nvtx --nvtx-include "<label>/")."""
     for _ in range(warmup):
         sysm.solve(bt, xt)
     torch.cuda.synchronize()
@@ -249,9 +251,11 @@ def time_solves(torch, sysm, bt, xt, steps, warmup, flush, stream):
     t0 = time.perf_counter()
     for i in range(steps):
         flush.zero_()
+        torch.cuda.nvtx.range_push(label)
         starts[i].record(stream)
         sysm.solve(bt, xt)
         ends[i].record(stream)
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -302,8 +306,8 @@ def run_ours(args):
     clocks.start()
     torch.cuda.synchronize()
     region0 = time.perf_counter()
-    ms_plain, _ = time_solves(torch, plain, bt, xp, args.steps, args.warmup, flush, stream)
-    ms_rw, wall_rw = time_solves(torch, rw, bt, xr, args.steps, args.warmup, flush, stream)
+    ms_plain, _ = time_solves(torch, plain, bt, xp, args.steps, args.warmup, flush, stream, "timed_plain")
+    ms_rw, wall_rw = time_solves(torch, rw, bt, xr, args.steps, args.warmup, flush, stream, "timed_rewritten")
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()

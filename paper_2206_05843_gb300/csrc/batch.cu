@@ -158,7 +158,7 @@ sptrsv_status layout_batch(sptrsv_batch* bt, int lpr_mode) {
         it.blk0 = (int)blocks.size();
         if (s->m > 0 &&
             build_run_blocks(s->lv.h_level_ptr.data(), bt->hcptr[i].data(), 0, s->m, g.stage_rows, g.stage_entries,
-                             it.lpr, blocks) != 0) {
+                             it.lpr, nr, fast_rec_capacity(vb, g), blocks) != 0) {
             set_error("batch: system %d has a row with more coefficients than the staging area", i);
             return SPTRSV_ERR_UNSUPPORTED;
         }

@@ -8,9 +8,17 @@
 //           every row (dinv_r b_r plus the rewritten rows' E row times b);
 //   stage B (after every x the block reads from outside the ring is final): each
 //           coefficient whose dependency is older than the ring window is applied to the
-//           b-part right away; the others are compacted with their ring slot;
+//           b-part right away; the others are compacted with their ring slot, or, in a
+//           fast block, laid out as one record per lane and FMA step (below);
 //   compute: per level, rows read x only from the shared-memory ring;
 //   write-out: the block's x leaves the ring once, coalesced.
+//
+// Fast blocks.  An SM runs at most four float64 warp instructions at a time, each for ~64
+// cycles, and a predicated-off one still takes its slot.  A fast block (one right-hand
+// side, every level within 32 lanes, at most K_MAX FMAs per lane) therefore runs exactly K
+// FMAs per lane and level, K fixed for the block: the staging pads each lane to K records
+// {coefficient, ring slot} with {0, zero slot}, and warp 0 runs a branch-free loop whose
+// per-level metadata is loaded one level ahead.
 #pragma once
 
 #include "system.cuh"
@@ -79,9 +87,33 @@ inline size_t run_stage_bytes(int vb, int nrhs, const RunGeom& g) {
     return (size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) + (size_t)(3 * g.stage_rows + 2) * 4;
 }
 
+// the ring holds ring_rows x nrhs values plus RING_PAD spare values: the zero slot (read by
+// the padding records of fast blocks, always 0) and the dummy slot (written by their idle lanes)
+constexpr int RING_PAD = 4;
+
 // the x ring plus two staging buffers (one is filled while the other is computed)
 inline size_t run_smem_bytes(int vb, int nrhs, const RunGeom& g) {
-    return (size_t)g.ring_rows * nrhs * vb + 2 * ((run_stage_bytes(vb, nrhs, g) + 15) / 16 * 16);
+    return ((size_t)g.ring_rows * nrhs + RING_PAD) * vb + 2 * ((run_stage_bytes(vb, nrhs, g) + 15) / 16 * 16);
+}
+
+// one FMA step of one lane of a fast block: coefficient and ring slot of the dependency
+template <typename T>
+struct FastRec;
+template <>
+struct __align__(16) FastRec<double> {
+    double cv;
+    int32_t slot, pad;
+};
+template <>
+struct __align__(8) FastRec<float> {
+    float cv;
+    int32_t slot;
+};
+
+// records a staging buffer holds: they reuse the area of the compacted coefficients
+inline int fast_rec_capacity(int vb, const RunGeom& g) {
+    const int64_t bytes = (int64_t)g.stage_entries * (vb + 4) - 16;
+    return bytes > 0 ? (int)(bytes / (vb == 8 ? 16 : 8)) : 0;
 }
 
 template <typename T>
@@ -90,20 +122,26 @@ struct RunSmem {
     T* bp;
     T* cval;
     int32_t* cslot;
+    FastRec<T>* rec;  // fast blocks: aliases cval / cslot
     int32_t* cptr;
     int32_t* row;
     int32_t* lp;
     RunGeom g;
+    int zero_slot;    // ring index that always holds 0
+    int dummy_slot;   // ring index that idle lanes write
     // buffer 0 or 1 of the staging area; the ring is shared
     __device__ void carve(unsigned char* base, int nrhs, RunGeom geo, int buf = 0) {
         g = geo;
         ring = (T*)base;
+        zero_slot = g.ring_rows * nrhs;
+        dummy_slot = zero_slot + 1;
         const size_t vb = sizeof(T);
         const size_t stage = ((size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) +
                               (size_t)(3 * g.stage_rows + 2) * 4 + 15) / 16 * 16;
-        bp = (T*)(base + (size_t)g.ring_rows * nrhs * vb + buf * stage);
+        bp = (T*)(base + ((size_t)g.ring_rows * nrhs + RING_PAD) * vb + buf * stage);
         cval = bp + (size_t)g.stage_rows * nrhs;
         cslot = (int32_t*)(cval + g.stage_entries);
+        rec = (FastRec<T>*)(((uintptr_t)cval + 15) & ~(uintptr_t)15);
         cptr = cslot + g.stage_entries;
         row = cptr + g.stage_rows + 1;
         lp = row + g.stage_rows;
@@ -112,9 +150,13 @@ struct RunSmem {
 
 // A block is a range of positions [P0, P1) covering nl consecutive levels from l0 (the
 // first and last of them possibly in part: the rows of one level are independent, so a
-// level too large for the staging area is split over consecutive blocks).
-// int4 {P0, P1, l0, nl | narrow << 30}
-constexpr int BLK_NARROW = 1 << 30;
+// level too large for the staging area is split over consecutive blocks; fast blocks hold
+// whole levels).  int4 {P0, P1, l0, nl | flags}
+constexpr int BLK_NARROW = 1 << 30;   // every level of the block fits 32 lanes
+constexpr int BLK_FAST = 1 << 29;     // fast block (narrow, one right-hand side, records)
+constexpr int BLK_K_SHIFT = 26;       // FMA steps per lane and level of a fast block, 1..K_MAX
+constexpr int BLK_NL_MASK = (1 << 26) - 1;
+constexpr int K_MAX = 4;
 
 // stage A: rows, level pointers (relative to P0) and the b-part; thread per row
 // a group of threads that stages a block: all threads of the CTA (barrier 0) or the
@@ -152,8 +194,58 @@ __device__ void run_stage_a(const SysView<T>& v, RunSmem<T>& sm, int l0, int nl,
 // b-part; compact the others with their ring slots.  Same thread-to-row mapping as
 // stage A, so the b-part needs no barrier in between.
 template <typename T>
+__device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int rows, int64_t ring_lo,
+                                 const Grp& G, int nl, int K, int lpr) {
+    const int mask = sm.g.ring_rows - 1;
+    const int steps = K * lpr;  // records per row
+    G.sync();                   // the level pointers of stage A, written by other threads
+    for (int i = G.tid; i < rows; i += G.nthr) {
+        // level of row i: the last li with lp[li] <= i
+        int lo = 0, hi = nl - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sm.lp[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const int lb = sm.lp[lo], le = sm.lp[lo + 1];
+        const int nlanes = (le - lb) * lpr;
+        // records of level lo start at K * lpr * lb; step u of lane (g * lpr + e) at u * nlanes + lane
+        FastRec<T>* r = sm.rec + (size_t)K * lpr * lb + (size_t)(i - lb) * lpr;
+        const int64_t p = P0 + i;
+        const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
+        T bp = sm.bp[i];
+        int j = 0;
+        for (int q = q0; q < q1; ++q) {
+            const int32_t d = v.ccol[q];
+            const T c = v.cval[q];
+            if (d >= ring_lo) {
+                if (j < steps) {
+                    FastRec<T>& e = r[(j / lpr) * nlanes + (j % lpr)];
+                    e.cv = c;
+                    e.slot = d & mask;
+                }
+                ++j;
+            } else {
+                bp -= c * __ldcg(v.xp + d);
+            }
+        }
+        for (; j < steps; ++j) {
+            FastRec<T>& e = r[(j / lpr) * nlanes + (j % lpr)];
+            e.cv = T(0);
+            e.slot = sm.zero_slot;
+        }
+        sm.bp[i] = bp;
+    }
+    G.sync();
+}
+
+template <typename T>
 __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int rows, int64_t ring_lo,
-                            const Grp& G) {
+                            const Grp& G, int nl, int blk_flags, int lpr) {
+    if (blk_flags & BLK_FAST) {
+        run_stage_b_fast(v, sm, P0, rows, ring_lo, G, nl, (blk_flags >> BLK_K_SHIFT) & 7, lpr);
+        return;
+    }
     const int nrhs = v.nrhs;
     const int mask = sm.g.ring_rows - 1;
     for (int i = G.tid; i < rows; i += G.nthr) {
@@ -207,79 +299,96 @@ __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int
     G.sync();
 }
 
-// Narrow block, one right-hand side, LPR lanes per row (LPR = 1, 2 or 4): every lane
-// holds up to NK of its row's coefficients (entries el, el+LPR, ...) and their ring slots
-// in registers, read for the next level while the current level computes; the lanes of
-// a row combine their partial sums with shuffles.  A level costs its ring loads plus
-// ceil(deps / LPR) dependent float64 FMAs and log2(LPR) adds.
-constexpr int NK = 4;  // coefficients per lane held in registers
-
-template <typename T>
-struct RowRegs {
-    int i, c0, c1;
-    bool act;
+// Fast block compute, warp 0.  Lane (g * LPR + e) of a level takes row g of the level and
+// its FMA steps e, e + LPR, ...: K records, its row's b-part on e = 0, the ring load of each
+// dependency, K float64 FMAs, log2(LPR) shuffle adds, one store.  The records of level li + 1
+// are loaded while level li computes (two register sets, alternating), and the level pointers
+// two levels ahead.
+template <typename T, int K>
+struct FastOps {
+    int slot[K];
+    T cv[K];
     T bp;
-    int slot[NK];
+    int out;
 };
 
-template <typename T, int LPR>
-__device__ __forceinline__ void load_row_regs(const RunSmem<T>& sm, int lb, int le, RowRegs<T>& r) {
-    const int el = (int)threadIdx.x & (LPR - 1);
-    r.i = lb + (int)threadIdx.x / LPR;
-    r.act = r.i < le;
-    r.c0 = r.act ? sm.cptr[r.i] : 0;
-    r.c1 = r.act ? sm.cptr[r.i + 1] : 0;
-    r.bp = (r.act && el == 0) ? sm.bp[r.i] : T(0);
+template <typename T, int LPR, int K>
+__device__ __forceinline__ void fast_load(const RunSmem<T>& sm, int64_t P0, int mask, int lb, int le,
+                                          FastOps<T, K>& o) {
+    const int lane = (int)threadIdx.x;
+    const int nlanes = (le - lb) * LPR;
+    const bool act = lane < nlanes;
+    const FastRec<T>* r = sm.rec + (size_t)K * LPR * lb + lane;
 #pragma unroll
-    for (int u = 0; u < NK; ++u) {
-        const int q = r.c0 + el + u * LPR;
-        r.slot[u] = q < r.c1 ? sm.cslot[q] : 0;
+    for (int u = 0; u < K; ++u) {
+        if (act) {
+            const FastRec<T> e = r[u * nlanes];
+            o.slot[u] = e.slot;
+            o.cv[u] = e.cv;
+        } else {
+            o.slot[u] = sm.zero_slot;
+            o.cv[u] = T(0);
+        }
     }
+    const int i = lb + lane / LPR;
+    const bool head = act && (lane & (LPR - 1)) == 0;
+    o.bp = head ? sm.bp[i] : T(0);
+    o.out = head ? (int)((P0 + i) & mask) : sm.dummy_slot;
 }
 
-template <typename T, int LPR>
-__device__ void run_compute_narrow(RunSmem<T>& sm, int64_t P0, int l0, int nl, unsigned long long* stamps) {
+template <typename T, int LPR, int K>
+__device__ __forceinline__ void fast_level(RunSmem<T>& sm, const FastOps<T, K>& o) {
+    T xv[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) xv[u] = sm.ring[o.slot[u]];
+    T acc = o.bp;
+#pragma unroll
+    for (int u = 0; u < K; ++u) acc -= o.cv[u] * xv[u];
+#pragma unroll
+    for (int sh = 1; sh < LPR; sh <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sh);
+    sm.ring[o.out] = acc;
+    __syncwarp();
+}
+
+template <typename T, int LPR, int K>
+__device__ void run_compute_fast(RunSmem<T>& sm, int64_t P0, int l0, int nl, unsigned long long* stamps) {
     if (threadIdx.x >= 32) return;
     const int mask = sm.g.ring_rows - 1;
-    const int el = (int)threadIdx.x & (LPR - 1);
-    RowRegs<T> cur, nxt;
-    load_row_regs<T, LPR>(sm, sm.lp[0], sm.lp[1], cur);
-    for (int li = 0; li < nl; ++li) {
-        if (li + 1 < nl) load_row_regs<T, LPR>(sm, sm.lp[li + 1], sm.lp[li + 2], nxt);
-        T acc = cur.bp;
-        if (cur.act) {
-            T xv[NK], cv[NK];
-#pragma unroll
-            for (int u = 0; u < NK; ++u) {
-                const int q = cur.c0 + el + u * LPR;
-                xv[u] = sm.ring[cur.slot[u]];
-                cv[u] = q < cur.c1 ? sm.cval[q] : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < NK; ++u)
-                if (cur.c0 + el + u * LPR < cur.c1) acc -= cv[u] * xv[u];
-            for (int q = cur.c0 + el + NK * LPR; q < cur.c1; q += LPR) acc -= sm.cval[q] * sm.ring[sm.cslot[q]];
-        }
-#pragma unroll
-        for (int o = 1; o < LPR; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (cur.act && el == 0) sm.ring[(int)((P0 + cur.i) & mask)] = acc;
-        __syncwarp();
+    auto lpb = [&](int li) { return li < nl ? sm.lp[li] : 0; };
+    auto lpe = [&](int li) { return li < nl ? sm.lp[li + 1] : 0; };
+    FastOps<T, K> oa, ob;
+    int b1 = lpb(1), e1 = lpe(1), b2 = lpb(2), e2 = lpe(2);
+    fast_load<T, LPR, K>(sm, P0, mask, lpb(0), lpe(0), oa);
+    for (int li = 0; li < nl; li += 2) {
+        const int b3 = lpb(li + 3), e3 = lpe(li + 3);
+        fast_load<T, LPR, K>(sm, P0, mask, b1, e1, ob);
+        fast_level<T, LPR, K>(sm, oa);
         if (stamps && threadIdx.x == 0) stamps[l0 + li] = globaltimer();
-        cur = nxt;
+        if (li + 1 >= nl) break;
+        const int b4 = lpb(li + 4), e4 = lpe(li + 4);
+        fast_load<T, LPR, K>(sm, P0, mask, b2, e2, oa);
+        fast_level<T, LPR, K>(sm, ob);
+        if (stamps && threadIdx.x == 0) stamps[l0 + li + 1] = globaltimer();
+        b1 = b3; e1 = e3; b2 = b4; e2 = e4;
+    }
+}
+
+template <typename T, int LPR>
+__device__ void run_compute_fast_k(RunSmem<T>& sm, int K, int64_t P0, int l0, int nl, unsigned long long* stamps) {
+    switch (K) {
+        case 1: run_compute_fast<T, LPR, 1>(sm, P0, l0, nl, stamps); break;
+        case 2: run_compute_fast<T, LPR, 2>(sm, P0, l0, nl, stamps); break;
+        case 3: run_compute_fast<T, LPR, 3>(sm, P0, l0, nl, stamps); break;
+        default: run_compute_fast<T, LPR, 4>(sm, P0, l0, nl, stamps); break;
     }
 }
 
 template <typename T>
-__device__ __forceinline__ bool narrow_fast(const Lanes& ln, int nrhs) {
-    return nrhs == 1 && (ln.lpr == 1 || ln.lpr == 2 || ln.lpr == 4);
-}
-
-template <typename T>
-__device__ void run_compute_narrow_any(RunSmem<T>& sm, const Lanes& ln, int64_t P0, int l0, int nl,
-                                       unsigned long long* stamps) {
-    if (ln.lpr == 1) run_compute_narrow<T, 1>(sm, P0, l0, nl, stamps);
-    else if (ln.lpr == 2) run_compute_narrow<T, 2>(sm, P0, l0, nl, stamps);
-    else run_compute_narrow<T, 4>(sm, P0, l0, nl, stamps);
+__device__ void run_compute_fast_any(RunSmem<T>& sm, int lpr, int K, int64_t P0, int l0, int nl,
+                                     unsigned long long* stamps) {
+    if (lpr == 1) run_compute_fast_k<T, 1>(sm, K, P0, l0, nl, stamps);
+    else if (lpr == 2) run_compute_fast_k<T, 2>(sm, K, P0, l0, nl, stamps);
+    else run_compute_fast_k<T, 4>(sm, K, P0, l0, nl, stamps);
 }
 
 // the level loop of one staged block; narrow blocks run on warp 0 alone
@@ -345,11 +454,13 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
     {
         RunSmem<T> s0;
         s0.carve(smem, v.nrhs, geo, 0);
+        if (threadIdx.x < RING_PAD) s0.ring[s0.zero_slot + threadIdx.x] = T(0);
         const int4 bd = blocks[blk0];
         __syncthreads();
-        run_stage_a(v, s0, bd.z, bd.w & (BLK_NARROW - 1), bd.x, bd.y, grp_all());
+        run_stage_a(v, s0, bd.z, bd.w & BLK_NL_MASK, bd.x, bd.y, grp_all());
         if (!wait()) return false;
-        run_stage_b(v, s0, bd.x, bd.y - bd.x, max(run_p0, (int64_t)bd.y - R), grp_all());
+        run_stage_b(v, s0, bd.x, bd.y - bd.x, max(run_p0, (int64_t)bd.y - R), grp_all(), bd.w & BLK_NL_MASK, bd.w,
+                    ln.lpr);
     }
     for (int blk = blk0; blk < blk1; ++blk) {
         const int par = (blk - blk0) & 1;
@@ -357,13 +468,13 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
         cur.carve(smem, v.nrhs, geo, par);
         const int4 bd = blocks[blk];
         const int64_t P0 = bd.x;
-        const int nl = bd.w & (BLK_NARROW - 1);
+        const int nl = bd.w & BLK_NL_MASK;
         const bool narrow = (bd.w & BLK_NARROW) != 0;
+        const bool fast = (bd.w & BLK_FAST) != 0;
         const bool next = blk + 1 < blk1;
-        const bool fast = narrow && narrow_fast<T>(ln, v.nrhs);
         const bool overlap = fast && next && blockDim.x > 32;
         if (!overlap || threadIdx.x < 32) {
-            if (fast) run_compute_narrow_any(cur, ln, P0, bd.z, nl, stamps);
+            if (fast) run_compute_fast_any(cur, ln.lpr, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
             else run_compute(v, cur, ln, narrow, P0, bd.z, nl, stamps);
         }
         if (!overlap) __syncthreads();
@@ -373,8 +484,8 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
             nx.carve(smem, v.nrhs, geo, par ^ 1);
             const int4 bn = blocks[blk + 1];
             const Grp G = overlap ? grp_stagers() : grp_all();
-            run_stage_a(v, nx, bn.z, bn.w & (BLK_NARROW - 1), bn.x, bn.y, G);
-            run_stage_b(v, nx, bn.x, bn.y - bn.x, max(run_p0, (int64_t)bn.y - R), G);
+            run_stage_a(v, nx, bn.z, bn.w & BLK_NL_MASK, bn.x, bn.y, G);
+            run_stage_b(v, nx, bn.x, bn.y - bn.x, max(run_p0, (int64_t)bn.y - R), G, bn.w & BLK_NL_MASK, bn.w, ln.lpr);
         }
         if (overlap) __syncthreads();
         run_write_out(v, cur, P0, (int)(bd.y - bd.x));
@@ -383,8 +494,10 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
     return true;
 }
 
-// host: cuts levels [l_begin, l_end) into staged blocks
+// host: cuts levels [l_begin, l_end) into staged blocks; levels that qualify (one
+// right-hand side, lpr 1, 2 or 4, at most 32 lanes, at most K_MAX FMA steps per lane) go to
+// fast blocks of at most fast_recs records (0: no fast blocks)
 int build_run_blocks(const int32_t* lp, const int32_t* cptr, int64_t l_begin, int64_t l_end, int stage_rows,
-                     int stage_entries, int lpr, std::vector<int4>& out);
+                     int stage_entries, int lpr, int nrhs, int fast_recs, std::vector<int4>& out);
 
 }  // namespace sp

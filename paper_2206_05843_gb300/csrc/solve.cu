@@ -89,20 +89,71 @@ int pow2_floor(int64_t v) {
 }  // namespace
 
 // Cuts levels [l_begin, l_end) into blocks that fit the staging area: whole levels while
-// they fit, a level that does not fit is split by rows.  Returns 0, or -1 when a single
-// row has more coefficients than the staging area holds.
+// they fit, a level that does not fit is split by rows.  Runs of levels that qualify for the
+// fast executor form fast blocks of whole levels; the block's FMA steps per lane K is the
+// largest ceil(row length / lpr) of its levels (an upper bound: dependencies older than the
+// ring are folded into the b-part at staging).  Returns 0, or -1 when a single row has more
+// coefficients than the staging area holds.
 int build_run_blocks(const int32_t* lp, const int32_t* cptr, int64_t l_begin, int64_t l_end, int stage_rows,
-                     int stage_entries, int lpr, std::vector<int4>& out) {
+                     int stage_entries, int lpr, int nrhs, int fast_recs, std::vector<int4>& out) {
+    const bool fast_on = fast_recs > 0 && nrhs == 1 && (lpr == 1 || lpr == 2 || lpr == 4);
+    // FMA steps a level needs in a fast block, or 0 when the level does not qualify
+    auto fast_k = [&](int64_t l) -> int {
+        if (!fast_on) return 0;
+        const int64_t rows = lp[l + 1] - lp[l];
+        if (rows * lpr > 32) return 0;
+        int64_t mx = 0;
+        for (int64_t i = lp[l]; i < lp[l + 1]; ++i) mx = std::max<int64_t>(mx, (int64_t)cptr[i + 1] - cptr[i]);
+        const int64_t k = std::max<int64_t>(1, (mx + lpr - 1) / lpr);
+        return k <= K_MAX ? (int)k : 0;
+    };
     int64_t P = lp[l_begin];
     const int64_t Pend = lp[l_end];
     int64_t l = l_begin;
+    int next_k = -1;  // fast_k of level l when already known
     while (P < Pend) {
-        while (lp[l + 1] <= P) ++l;
+        while (lp[l + 1] <= P) {
+            ++l;
+            next_k = -1;
+        }
+        if (P == lp[l]) {
+            int k0 = next_k >= 0 ? next_k : fast_k(l);
+            next_k = -1;
+            if (k0 > 0) {
+                // a fast block: whole levels while the records fit
+                int K = k0;
+                int64_t rows = lp[l + 1] - lp[l];
+                int64_t l1 = l + 1;
+                while (l1 < l_end) {
+                    const int kl = fast_k(l1);
+                    if (kl == 0) {
+                        next_k = 0;
+                        break;
+                    }
+                    const int64_t r = lp[l1 + 1] - lp[l1];
+                    const int Kn = std::max(K, kl);
+                    if (rows + r > stage_rows || (int64_t)Kn * lpr * (rows + r) > fast_recs) {
+                        next_k = kl;
+                        break;
+                    }
+                    rows += r;
+                    K = Kn;
+                    ++l1;
+                }
+                out.push_back(make_int4((int)P, (int)lp[l1], (int)l, (int)(l1 - l) | BLK_NARROW | BLK_FAST |
+                                                                         (K << BLK_K_SHIFT)));
+                P = lp[l1];
+                l = l1;
+                continue;
+            }
+        }
         const int64_t P0 = P, l0 = l;
         int64_t rows = 0, ents = 0, maxw = 0;
         int64_t lcur = l;
         while (P < Pend) {
             while (lp[lcur + 1] <= P) ++lcur;
+            // a level that qualifies for a fast block starts a block of its own
+            if (rows > 0 && fast_on && P == lp[lcur] && fast_k(lcur) > 0) break;
             const int64_t lend = lp[lcur + 1];
             const int64_t r = lend - P, e = (int64_t)cptr[lend] - cptr[P];
             if (rows + r <= stage_rows && ents + e <= stage_entries) {
@@ -200,7 +251,9 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
             int64_t l1 = l;
             while (l1 < m && thin(l1)) ++l1;
             int blk0 = (int)sc.h_blocks.size();
-            if (build_run_blocks(lp.data(), hcptr.data(), l, l1, stage_rows, stage_entries, lpr, sc.h_blocks) != 0) {
+            if (build_run_blocks(lp.data(), hcptr.data(), l, l1, stage_rows, stage_entries, lpr, nrhs,
+                                 fast_rec_capacity(vb, RunGeom{ring_rows, stage_rows, stage_entries}),
+                                 sc.h_blocks) != 0) {
                 set_error("schedule: a row has more coefficients than the staging area");
                 return SPTRSV_ERR_UNSUPPORTED;
             }
