@@ -234,9 +234,10 @@ def build_systems(B, M, lv, strategy: str):
 
 
 def launches_per_solve(sysm) -> int:
-    """Kernels of this library one solve launches: one persistent kernel, or one kernel
-    per level when the autotuner chose per-level launches."""
-    return int(sysm.m) if sysm.run_width() == -2 else 1
+    """Kernels of this library one solve launches (as the library reports them): the
+    persistent kernel, plus the b-part kernel for rewritten rows in staged blocks, or one
+    kernel per level when the autotuner chose per-level launches."""
+    return int(sysm.refresh()["launches"])
 
 
 def time_solves(torch, sysm, bt, xt, steps, warmup, flush, stream, label):

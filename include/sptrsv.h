@@ -171,6 +171,8 @@ typedef struct {
     int32_t run_width;     /*   widest level inside a single-CTA run (0 auto, -1 none, -2 one launch per level), */
     int32_t lanes_per_row; /*   lanes per row (0 auto) */
     int32_t strategy_used; /* SPTRSV_STRATEGY_* that produced the stored plan (LEARNED resolves to CHOSEN or NAIVE) */
+    int32_t launches;      /* kernels one single-RHS solve launches with the current schedule (0 before the
+                              first solve or tune) */
 } sptrsv_system_info;
 
 sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);

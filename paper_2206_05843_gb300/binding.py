@@ -66,7 +66,8 @@ class SystemInfo(C.Structure):
                 ("rows_moved", C.c_int64), ("stored_nnz", C.c_int64), ("nnz_l", C.c_int64),
                 ("segments", C.c_int64), ("run_levels", C.c_int64), ("dtype", C.c_int32),
                 ("rewritten", C.c_int32), ("avg_cost", C.c_double), ("block", C.c_int32),
-                ("run_width", C.c_int32), ("lanes_per_row", C.c_int32), ("strategy_used", C.c_int32)]
+                ("run_width", C.c_int32), ("lanes_per_row", C.c_int32), ("strategy_used", C.c_int32),
+                ("launches", C.c_int32)]
 
 
 class BatchInfo(C.Structure):

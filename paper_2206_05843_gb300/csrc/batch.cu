@@ -48,7 +48,8 @@ __device__ void run_item(const BatchItem& it, const int4* blocks, const void* b,
                  (const T*)it.eval,
                  (const T*)b,
                  (T*)x,
-                 (T*)it.xp};
+                 (T*)it.xp,
+                 nullptr};
     const Lanes ln = make_lanes(it.lpr, it.nrhs);
     run_blocks(v, smem, RunGeom{it.ring_rows, it.stage_rows, it.stage_entries}, ln, blocks, it.blk0, it.blk1,
                []() { return true; }, nullptr);

@@ -66,6 +66,7 @@ struct SysView {
     const T* __restrict__ b;
     T* x;
     T* xp;  // x in stored order, position-major: xp[p * nrhs + k]
+    const T* bpre;  // b-parts computed before the solve, indexed like xp; nullptr: staging computes them
 };
 
 // b-part of row p for right-hand side k: dinv_p b_row + sum over the E row
@@ -186,7 +187,11 @@ __device__ void run_stage_a(const SysView<T>& v, RunSmem<T>& sm, int l0, int nl,
         const int64_t p = P0 + i;
         const int32_t row = v.perm[p];
         sm.row[i] = row;
-        for (int k = 0; k < nrhs; ++k) sm.bp[(size_t)i * nrhs + k] = bpart_full(v, p, row, k);
+        if (v.bpre) {
+            for (int k = 0; k < nrhs; ++k) sm.bp[(size_t)i * nrhs + k] = __ldcg(v.bpre + p * nrhs + k);
+        } else {
+            for (int k = 0; k < nrhs; ++k) sm.bp[(size_t)i * nrhs + k] = bpart_full(v, p, row, k);
+        }
     }
 }
 
@@ -213,20 +218,33 @@ __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0
         FastRec<T>* r = sm.rec + (size_t)K * lpr * lb + (size_t)(i - lb) * lpr;
         const int64_t p = P0 + i;
         const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
+        // a fast row has at most K * lpr entries: its loads go out QC at a time
+        constexpr int QC = 8;
         T bp = sm.bp[i];
         int j = 0;
-        for (int q = q0; q < q1; ++q) {
-            const int32_t d = v.ccol[q];
-            const T c = v.cval[q];
-            if (d >= ring_lo) {
-                if (j < steps) {
-                    FastRec<T>& e = r[(j / lpr) * nlanes + (j % lpr)];
-                    e.cv = c;
-                    e.slot = d & mask;
+        for (int qb = q0; qb < q1; qb += QC) {
+            int32_t dd[QC];
+            T cc[QC];
+#pragma unroll
+            for (int u = 0; u < QC; ++u) {
+                const bool ok = qb + u < q1;
+                dd[u] = ok ? v.ccol[qb + u] : -1;
+                cc[u] = ok ? v.cval[qb + u] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < QC; ++u) {
+                if (qb + u >= q1) break;
+                const int32_t d = dd[u];
+                if (d >= ring_lo) {
+                    if (j < steps) {
+                        FastRec<T>& e = r[(j / lpr) * nlanes + (j % lpr)];
+                        e.cv = cc[u];
+                        e.slot = d & mask;
+                    }
+                    ++j;
+                } else {
+                    bp -= cc[u] * __ldcg(v.xp + d);
                 }
-                ++j;
-            } else {
-                bp -= c * __ldcg(v.xp + d);
             }
         }
         for (; j < steps; ++j) {
@@ -427,11 +445,11 @@ __device__ void run_compute(const SysView<T>& v, RunSmem<T>& sm, const Lanes& ln
 
 // x of the block leaves the ring: coalesced into xp, scattered into the caller's x
 template <typename T>
-__device__ void run_write_out(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int rows) {
+__device__ void run_write_out(const SysView<T>& v, const RunSmem<T>& sm, int64_t P0, int rows, const Grp& G) {
     const int nrhs = v.nrhs;
     const int mask = sm.g.ring_rows - 1;
     const int total = rows * nrhs;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    for (int t = G.tid; t < total; t += G.nthr) {
         const int i = t / nrhs, k = t - i * nrhs;
         const T val = sm.ring[(size_t)((P0 + i) & mask) * nrhs + k];
         __stcg(v.xp + (P0 + i) * nrhs + k, val);
@@ -440,11 +458,11 @@ __device__ void run_write_out(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, i
 }
 
 // Runs blocks [blk0, blk1).  `wait` is called once, after the first block's stage A.
-// Iteration of block i: compute block i (buffer i % 2) while -- when block i is narrow and
-// single-RHS -- warps 1.. stage block i+1 into the other buffer; then every thread writes
-// block i's x out of the ring.  Block i+1's stage B reads x only of blocks <= i-1 (a
-// dependency inside block i is always inside the ring window), which iteration i-1
-// wrote out.
+// Iteration of block i (buffer i % 2): compute block i; meanwhile -- when block i is a fast
+// block, on warps 1.. while warp 0 computes; otherwise on all threads, before and after the
+// compute -- write block i-1's x out of the ring and stage block i+1 into the other buffer.
+// Stage B of block i+1 reads from xp only x older than the ring window, which lies in
+// blocks <= i-1 (two blocks fit the ring), written out just before.
 template <typename T, typename WaitFn>
 __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo, const Lanes& ln, const int4* blocks,
                            int blk0, int blk1, WaitFn wait, unsigned long long* stamps) {
@@ -464,31 +482,59 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
     }
     for (int blk = blk0; blk < blk1; ++blk) {
         const int par = (blk - blk0) & 1;
-        RunSmem<T> cur;
+        RunSmem<T> cur, oth;
         cur.carve(smem, v.nrhs, geo, par);
+        oth.carve(smem, v.nrhs, geo, par ^ 1);
         const int4 bd = blocks[blk];
         const int64_t P0 = bd.x;
         const int nl = bd.w & BLK_NL_MASK;
         const bool narrow = (bd.w & BLK_NARROW) != 0;
         const bool fast = (bd.w & BLK_FAST) != 0;
+        const bool prev = blk > blk0;
         const bool next = blk + 1 < blk1;
-        const bool overlap = fast && next && blockDim.x > 32;
-        if (!overlap || threadIdx.x < 32) {
-            if (fast) run_compute_fast_any(cur, ln.lpr, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
-            else run_compute(v, cur, ln, narrow, P0, bd.z, nl, stamps);
+        const bool overlap = fast && blockDim.x > 32 && (prev || next);
+        if (overlap) {
+            if (threadIdx.x < 32) {
+                run_compute_fast_any(cur, ln.lpr, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
+            } else {
+                const Grp G = grp_stagers();
+                if (prev) {
+                    const int4 bp = blocks[blk - 1];
+                    run_write_out(v, oth, bp.x, (int)(bp.y - bp.x), G);
+                    G.sync();
+                }
+                if (next) {
+                    const int4 bn = blocks[blk + 1];
+                    run_stage_a(v, oth, bn.z, bn.w & BLK_NL_MASK, bn.x, bn.y, G);
+                    run_stage_b(v, oth, bn.x, bn.y - bn.x, max(run_p0, (int64_t)bn.y - R), G, bn.w & BLK_NL_MASK,
+                                bn.w, ln.lpr);
+                }
+            }
+        } else {
+            if (prev) {
+                const int4 bp = blocks[blk - 1];
+                run_write_out(v, oth, bp.x, (int)(bp.y - bp.x), grp_all());
+            }
+            if (fast) {
+                if (threadIdx.x < 32) run_compute_fast_any(cur, ln.lpr, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
+            } else {
+                run_compute(v, cur, ln, narrow, P0, bd.z, nl, stamps);
+            }
+            __syncthreads();
+            if (next) {
+                const int4 bn = blocks[blk + 1];
+                run_stage_a(v, oth, bn.z, bn.w & BLK_NL_MASK, bn.x, bn.y, grp_all());
+                run_stage_b(v, oth, bn.x, bn.y - bn.x, max(run_p0, (int64_t)bn.y - R), grp_all(), bn.w & BLK_NL_MASK,
+                            bn.w, ln.lpr);
+            }
         }
-        if (!overlap) __syncthreads();
-        if (next && (!overlap || threadIdx.x >= 32)) {
-            // stage the next block into the other buffer
-            RunSmem<T> nx;
-            nx.carve(smem, v.nrhs, geo, par ^ 1);
-            const int4 bn = blocks[blk + 1];
-            const Grp G = overlap ? grp_stagers() : grp_all();
-            run_stage_a(v, nx, bn.z, bn.w & BLK_NL_MASK, bn.x, bn.y, G);
-            run_stage_b(v, nx, bn.x, bn.y - bn.x, max(run_p0, (int64_t)bn.y - R), G, bn.w & BLK_NL_MASK, bn.w, ln.lpr);
-        }
-        if (overlap) __syncthreads();
-        run_write_out(v, cur, P0, (int)(bd.y - bd.x));
+        __syncthreads();
+    }
+    {
+        RunSmem<T> last;
+        last.carve(smem, v.nrhs, geo, (blk1 - 1 - blk0) & 1);
+        const int4 bl = blocks[blk1 - 1];
+        run_write_out(v, last, bl.x, (int)(bl.y - bl.x), grp_all());
         __syncthreads();
     }
     return true;

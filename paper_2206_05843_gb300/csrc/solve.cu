@@ -51,6 +51,7 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     a.lpr = sc.lpr;
     a.stage_rows = sc.stage_rows;
     a.stage_entries = sc.stage_entries;
+    a.pre = sc.pre;
 
     SP_CUDA(cudaMemsetAsync(s->flags.p, 0xff, (size_t)sc.grid * sizeof(int), st));
     SP_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
@@ -66,6 +67,7 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
         return SPTRSV_OK;
     }
     if (a.nseg == 0) return SPTRSV_OK;
+    if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)sc.grid);
     cfg.blockDim = dim3((unsigned)sc.block);
@@ -270,6 +272,10 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
             ++l;
         }
     }
+    // rewritten rows in thin levels: their b-parts (E rows) are computed up front by every
+    // CTA, so that staging reads one value per row instead of walking the E row
+    sc.pre = s->nnz_e > 0 && !sc.h_blocks.empty() && nrhs * (int64_t)vb <= 64 ? 1 : 0;
+    sc.pre_grid = (int)std::min<int64_t>((int64_t)sc.h_blocks.size(), (int64_t)sms * 8);
     if (sc.h_blocks.empty()) sc.h_blocks.push_back(make_int4(0, 0, 0, 0));
     SP_TRY(sc.segs.alloc(std::max<size_t>(1, sc.h_segs.size())));
     SP_TRY(sc.blocks.alloc(sc.h_blocks.size()));

@@ -238,6 +238,63 @@ __global__ void __launch_bounds__(256, 6) k_level(SolveArgs<T> a, int64_t p0, in
     a.x[(int64_t)row + (int64_t)k * a.ld] = acc;
 }
 
+// b-parts dinv_p b_row + E_p b of the rows of the staged blocks, written to xp (indexed like
+// x) before the solve, so that staging reads one value per row instead of walking its E row.
+// CTA me takes blocks me, me + gridDim.x, ...; a thread per row with at most LONG E entries
+// (four in flight at a time), then a warp per longer row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bparts(SolveArgs<T> a, int nblocks) {
+    constexpr int LONG = 64;
+    const int me = blockIdx.x, parts = gridDim.x;
+    const int nrhs = a.nrhs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int bi = me; bi < nblocks; bi += parts) {
+        const int4 bd = a.blocks[bi];
+        for (int64_t p = bd.x + threadIdx.x; p < bd.y; p += blockDim.x) {
+            const int e0 = a.eptr[p], e1 = a.eptr[p + 1];
+            if (e1 - e0 > LONG) continue;
+            const int32_t row = a.perm[p];
+            const T di = a.dinv[p];
+            for (int k = 0; k < nrhs; ++k) {
+                const int64_t ko = (int64_t)k * a.ld;
+                T acc = di * a.b[(int64_t)row + ko];
+                int q = e0;
+                for (; q + 4 <= e1; q += 4) {
+                    const int32_t c0 = a.ecol[q], c1 = a.ecol[q + 1], c2 = a.ecol[q + 2], c3 = a.ecol[q + 3];
+                    const T v0 = a.eval[q], v1 = a.eval[q + 1], v2 = a.eval[q + 2], v3 = a.eval[q + 3];
+                    const T b0 = a.b[c0 + ko], b1 = a.b[c1 + ko], b2 = a.b[c2 + ko], b3 = a.b[c3 + ko];
+                    acc += v0 * b0;
+                    acc += v1 * b1;
+                    acc += v2 * b2;
+                    acc += v3 * b3;
+                }
+                for (; q < e1; ++q) acc += a.eval[q] * a.b[a.ecol[q] + ko];
+                __stcg(a.xp + p * nrhs + k, acc);
+            }
+        }
+        for (int64_t base = bd.x + (int64_t)warp * 32; base < bd.y; base += (int64_t)nwarps * 32) {
+            const int64_t pl = base + lane;
+            const bool lng = pl < bd.y && a.eptr[pl + 1] - a.eptr[pl] > LONG;
+            unsigned mk = __ballot_sync(0xffffffffu, lng);
+            while (mk) {
+                const int src = __ffs(mk) - 1;
+                mk &= mk - 1;
+                const int64_t p = base + src;
+                const int e0 = a.eptr[p], e1 = a.eptr[p + 1];
+                const int32_t row = a.perm[p];
+                for (int k = 0; k < nrhs; ++k) {
+                    const int64_t ko = (int64_t)k * a.ld;
+                    T acc = T(0);
+                    for (int q = e0 + lane; q < e1; q += 32) acc += a.eval[q] * a.b[a.ecol[q] + ko];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) __stcg(a.xp + p * nrhs + k, a.dinv[p] * a.b[(int64_t)row + ko] + acc);
+                }
+            }
+        }
+    }
+}
+
 __global__ void k_stamp(unsigned long long* stamps, int64_t l) {
     if (threadIdx.x == 0) stamps[l] = globaltimer();
 }
@@ -272,8 +329,9 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
             if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
         } else {
             if (me != 0) continue;
-            SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval, a.dinv,
-                         a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp};
+            SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval,
+                         a.dinv, a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp,
+                         a.pre ? a.xp : nullptr};
             auto wait = [&]() { return wait_segment(a, s - 1); };
             if (!run_blocks(v, smem, RunGeom{a.ring_rows, a.stage_rows, a.stage_entries}, ln, a.blocks, sg.y, sg.z,
                             wait, a.stamps))

@@ -87,10 +87,12 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
     a.lpr = sc.lpr;
     a.stage_rows = sc.stage_rows;
     a.stage_entries = sc.stage_entries;
+    a.pre = sc.pre;
     SP_CUDA(cudaFuncSetAttribute(k_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.smem));
     SP_CUDA(cudaMemsetAsync(a.flags, 0xff, (size_t)sc.grid * sizeof(int), st));
     SP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
     if (a.nseg == 0) return SPTRSV_OK;
+    if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)sc.grid);
     cfg.blockDim = dim3((unsigned)sc.block);

@@ -221,6 +221,10 @@ sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info*
     o->run_width = s->run_width;
     o->lanes_per_row = s->lpr;
     o->strategy_used = s->strategy_used;
+    const sp::Schedule& sc = s->sched;
+    if (!sc.segs.p) o->launches = 0;
+    else if (sc.run_width == -2) o->launches = (int32_t)s->m;
+    else o->launches = sc.h_segs.empty() ? 0 : 1 + sc.pre;
     return SPTRSV_OK;
 }
 

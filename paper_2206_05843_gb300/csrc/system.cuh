@@ -5,6 +5,7 @@
 
 namespace sp {
 
+// WIDE: one level over CTAs 0..w-1; RUN: staged blocks [y, z) on CTA 0
 enum SegType : int { SEG_WIDE = 0, SEG_RUN = 1 };
 
 // A segment of the persistent solve.  WIDE: one level split over CTAs 0..parts-1.
@@ -17,6 +18,8 @@ enum SegType : int { SEG_WIDE = 0, SEG_RUN = 1 };
 struct Schedule {
     int nrhs = -1, block = 0, run_width = 0, lpr = 0, grid = 0, ring_rows = 0;
     int stage_rows = 0, stage_entries = 0;
+    int pre = 0;       // a b-part kernel runs before the solve (rewritten rows in staged blocks)
+    int pre_grid = 0;  // its CTAs
     size_t smem = 0;
     int64_t run_levels = 0;
     std::vector<int4> h_segs, h_blocks;
@@ -52,6 +55,7 @@ struct SolveArgs {
     int ring_rows;  // power of two
     int lpr;        // lanes per row (power of two <= 32)
     int stage_rows, stage_entries;
+    int pre;        // xp holds the b-parts of the staged blocks' rows (k_bparts ran first)
 };
 
 }  // namespace sp
