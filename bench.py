@@ -133,6 +133,26 @@ def make_workload(name):
     return m, b, xt
 
 
+FP64_LATENCY_CYCLES = 64  # dependent float64 operation on GB300 (clock64 measurement)
+
+
+def chain_floor(sysm, sm_mhz: float) -> dict:
+    """Dependency-chain floor of a level-set solve: every level needs, after its last
+    dependency is known, one product and a tree of ceil(log2 k) adds over the k coefficients
+    of its longest row -- each a dependent float64 operation of FP64_LATENCY_CYCLES cycles."""
+    ex = sysm.export()
+    lev = ex["level"].astype(np.int64)
+    deg = np.diff(ex["cptr"]).astype(np.int64)
+    m = int(sysm.m)
+    kmax = np.zeros(max(m, 1), np.int64)
+    np.maximum.at(kmax, lev, deg)
+    ops = np.where(kmax > 0, 1 + np.ceil(np.log2(np.maximum(kmax, 1))).astype(np.int64), 1)[:m]
+    total = int(ops.sum())
+    us = total * FP64_LATENCY_CYCLES / sm_mhz
+    return {"levels": m, "dependent_fp64_ops": total, "fp64_latency_cycles": FP64_LATENCY_CYCLES,
+            "sm_mhz": sm_mhz, "floor_us": round(us, 1)}
+
+
 STRATEGY_NAMES = {0: "none", 1: "naive", 2: "depth_k", 3: "learned", 4: "chosen depths", 5: "manual"}
 
 
@@ -362,6 +382,13 @@ def run_ours(args):
             traffic = json.load(open(tfile)).get(used)
         except (OSError, ValueError):
             traffic = None
+    sm_mhz = float(clk.get("sm_mhz") or 0) if isinstance(clk, dict) else 0.0
+    crit = chain_floor(rw, sm_mhz if sm_mhz > 0 else 2070.0)
+    crit["achieved_us"] = round(us_rw, 1)
+    crit["frac"] = round(crit["floor_us"] / us_rw, 4) if us_rw > 0 else None
+    crit_pl = chain_floor(plain, sm_mhz if sm_mhz > 0 else 2070.0)
+    crit["plain"] = {"floor_us": crit_pl["floor_us"], "achieved_us": round(us_plain, 1),
+                     "frac": round(crit_pl["floor_us"] / us_plain, 4) if us_plain > 0 else None}
     cpu = None
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
         us_cpu, count = cpu_oracle_time(m, b, args.cpu_seconds)
@@ -406,6 +433,7 @@ def run_ours(args):
                      "frac": round(gbs_rw / peak, 5), "traffic": traffic,
                      "peak_source": f"{peak_src} copy bandwidth", "kernel": "k_solve<double>",
                      "alg_bytes_per_launch": by_rw},
+        "critical_path": crit,
         "cpu_baseline": cpu,
         "e2e": {"value": round(us_e2e, 3), "unit": "us", "h2d_bytes_per_step": int(b.nbytes),
                 "d2h_bytes_per_step": int(b.nbytes)},
