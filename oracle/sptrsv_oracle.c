@@ -170,6 +170,8 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
 #define ORC_CHOSEN 3  /* per-target depth given by the caller (learned picker) */
 #define ORC_MANUAL 4  /* fixed distance over thin levels only: "every 9 levels into the 10th"
                          applied to the levels cheaper than avgLevelCost (Section IV) */
+#define ORC_CHOSEN_THIN 5  /* per-target depth over thin levels only: the learned picker's
+                              depth choice within the thin-level rule of Section III */
 
 /*
  * Walk the levels in order and decide, row by row, the level each row moves to.
@@ -197,10 +199,12 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
  *   becomes the next target.  The nnz cap rejects rows as in NAIVE.
  * MANUAL: thin levels are eligible as in NAIVE, levels join a target by distance as in
  *   DEPTH (no cost rule).
+ * CHOSEN_THIN: thin levels are eligible as in NAIVE, levels join a target by its own
+ *   distance depth_of_target[t] as in CHOSEN (no cost rule).
  *
  * inputs : lower-triangular CSR (diagonal last), level[n], m, kind, k, avg_override
  *          (<= 0: computed), cap_ratio (<= 0: no cap), injected_cost (NULL: computed),
- *          depth_of_target[m] (CHOSEN only)
+ *          depth_of_target[m] (CHOSEN and CHOSEN_THIN only)
  * outputs: target[n] (the level each row ends up on, in the original numbering),
  *          row_cost[n] (cost of each row on its final level under the planner's model),
  *          info[6] = {rows moved, nnz(L') + nnz(E explicit) after planning, nnz(L),
@@ -269,11 +273,13 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
     int32_t t = -1;
     int64_t cur = 0;
     for (int32_t s = 0; s < m; ++s) {
-        int eligible = (kind == ORC_NAIVE || kind == ORC_MANUAL) ? ((double)lcost[s] < avg) : 1;
+        int eligible = (kind == ORC_NAIVE || kind == ORC_MANUAL || kind == ORC_CHOSEN_THIN) ? ((double)lcost[s] < avg) : 1;
         if (!eligible) { t = -1; continue; }
         if (t < 0) { t = s; cur = lcost[s]; targets++; continue; }
         if ((kind == ORC_DEPTH || kind == ORC_MANUAL) && s - t > k) { t = s; cur = lcost[s]; targets++; continue; }
-        if (kind == ORC_CHOSEN && s - t > depth_of_target[t]) { t = s; cur = lcost[s]; targets++; continue; }
+        if ((kind == ORC_CHOSEN || kind == ORC_CHOSEN_THIN) && s - t > depth_of_target[t]) {
+            t = s; cur = lcost[s]; targets++; continue;
+        }
         for (int64_t q = lptr[s]; q < lptr[s + 1]; ++q) {
             int64_t r = byl[q];
             /* substitute every dependency on the target level or below it, until none

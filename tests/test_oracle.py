@@ -417,6 +417,31 @@ def test_planner_manual_is_depth_over_thin_levels():
     assert p.levels_after < mm
 
 
+def test_planner_chosen_thin_follows_per_target_depths_on_thin_levels():
+    """CHOSEN_THIN (the learned strategy's plan): thin levels only, as in the Section III
+    rule, each target taking the next depth_of_target[t] levels.  On a chain whose levels
+    are all thin the partition follows from the depths alone; with one depth k everywhere
+    it is the MANUAL plan with k, fat levels left alone."""
+    n = 60
+    chain = S.gen_from_deps(n, np.array([0] + [1] * (n - 1)), np.arange(n - 1), S.rng_for(4))
+    lev, mm = O.levels(chain.rowptr, chain.colidx)
+    dot = S.rng_for(5).integers(0, 5, mm).astype(np.int32)
+    p = O.plan(chain.rowptr, chain.colidx, lev, mm, O.CHOSEN_THIN, avg=100.0, depth_of_target=dot)
+    exp = np.empty(mm, np.int64)
+    t = -1
+    for lv_ in range(mm):
+        if t < 0 or lv_ - t > dot[t]:
+            t = lv_
+        exp[lv_] = t
+    assert np.array_equal(p.target, exp[lev])
+    m = S.gen_torso2_like(scale=0.25)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    for k in (3, 9):
+        p1 = O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN_THIN, depth_of_target=np.full(mm, k, np.int32))
+        p2 = O.plan(m.rowptr, m.colidx, lev, mm, O.MANUAL, k=k)
+        assert np.array_equal(p1.target, p2.target) and p1.moved == p2.moved > 0
+
+
 @pytest.mark.parametrize("alpha,beta", [(3, 0), (0, 40), (4, 100), (1, 0)])
 def test_planner_per_row_rules(alpha, beta):
     """Section III.A rules: every rewritten row keeps fewer than alpha dependencies and a
