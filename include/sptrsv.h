@@ -119,7 +119,8 @@ enum {
     SPTRSV_STRATEGY_NONE = 0,    /* no rewriting: same as sptrsv_system_plain */
     SPTRSV_STRATEGY_NAIVE = 1,   /* Section III avgLevelCost strategy over thin levels */
     SPTRSV_STRATEGY_DEPTH_K = 2, /* fixed distance: each target takes the next k levels (Section III, manual approach) */
-    SPTRSV_STRATEGY_LEARNED = 3, /* depth per target chosen by a trained picker (falls back to NAIVE without one) */
+    SPTRSV_STRATEGY_LEARNED = 3, /* thin levels (Section III) merged into targets at depths a trained picker
+                                    chooses per target (NAIVE without a picker) */
     SPTRSV_STRATEGY_CHOSEN = 4,  /* depth per target given by the caller */
     SPTRSV_STRATEGY_MANUAL = 5   /* fixed distance k over thin levels only: the manual approach of the earlier work
                                     ("every 9 levels into the 10th", Sections III and IV) */

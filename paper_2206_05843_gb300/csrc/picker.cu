@@ -381,7 +381,7 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
     if (m > 0) k_choose_depths<<<nblk(m, 256), 256, 0, st>>>(m, pred.as<float>(), dep.as<int32_t>(), nd, dot.as<int32_t>());
     SP_CUDA(cudaGetLastError());
     sptrsv_system* model = nullptr;
-    SP_TRY(rewrite_system(L, lv, 3 /* depth per target */, 0, dot.as<int32_t>(), sg->avg_override, sg->nnz_growth_cap,
+    SP_TRY(rewrite_system(L, lv, 5 /* depth per thin target */, 0, dot.as<int32_t>(), sg->avg_override, sg->nnz_growth_cap,
                           sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &model, st));
     model->strategy_used = SPTRSV_STRATEGY_CHOSEN;
     if (sg->learned_mode == 1) {

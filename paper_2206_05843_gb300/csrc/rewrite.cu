@@ -22,7 +22,9 @@
 namespace sp {
 
 // kinds of the walk
-enum { WALK_NAIVE = 1, WALK_DEPTH = 2, WALK_CHOSEN = 3, WALK_MANUAL = 4 };
+// CHOSEN_THIN: the learned strategy's plan -- thin levels only (Section III), each target
+// taking its own number of following levels
+enum { WALK_NAIVE = 1, WALK_DEPTH = 2, WALK_CHOSEN = 3, WALK_MANUAL = 4, WALK_CHOSEN_THIN = 5 };
 
 namespace {
 
@@ -116,13 +118,14 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
     int64_t cur = 0, stored = a.nnzL, moved = 0, targets = 0, top = 0;
     for (int64_t s = 0; s < a.m; ++s) {
         const int64_t ls = a.lcost[s];
-        const bool eligible = (a.kind == WALK_NAIVE || a.kind == WALK_MANUAL) ? ((double)ls < a.avg) : true;
+        const bool eligible =
+            (a.kind == WALK_NAIVE || a.kind == WALK_MANUAL || a.kind == WALK_CHOSEN_THIN) ? ((double)ls < a.avg) : true;
         if (!eligible) {
             t = -1;
             continue;
         }
         if (t < 0 || ((a.kind == WALK_DEPTH || a.kind == WALK_MANUAL) && s - t > a.k) ||
-            (a.kind == WALK_CHOSEN && s - t > a.dot[t])) {
+            ((a.kind == WALK_CHOSEN || a.kind == WALK_CHOSEN_THIN) && s - t > a.dot[t])) {
             t = (int)s;
             cur = ls;
             targets++;
@@ -480,7 +483,8 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
                            double avg, double cap, const int64_t* inj, int alpha, int64_t beta, int32_t* target,
                            PlanOut& po, cudaStream_t st) {
     const int64_t n = L->n, m = lv.m;
-    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || cap > 0 || inj || alpha > 0 || beta > 0;
+    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || kind == WALK_CHOSEN_THIN || cap > 0 || inj ||
+                      alpha > 0 || beta > 0;
     if (!walk) {
         Scratch lt;
         SP_TRY(lt.alloc(std::max<int64_t>(1, m) * sizeof(int32_t), st));

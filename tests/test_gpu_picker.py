@@ -110,9 +110,9 @@ def test_learned_rewrite_extremes_match_oracle_plans():
     # predictions all positive: no candidate helps, nothing is rewritten
     s0 = B.System(M, lv, B.LEARNED, cap=1.5, picker=constant_picker(1.0), model_only=True)
     assert s0.info["rows_moved"] == 0 and s0.m == mm
-    # all negative and equal: the first depth with the lowest prediction (the smallest)
+    # all negative and equal: the first depth with the lowest prediction (the smallest), on thin levels
     s1 = B.System(M, lv, B.LEARNED, cap=1.5, picker=constant_picker(-1.0), depths=[4, 8], model_only=True)
-    p = O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN, cap=1.5, depth_of_target=np.full(mm, 4))
+    p = O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN_THIN, cap=1.5, depth_of_target=np.full(mm, 4))
     assert np.array_equal(s1.export()["target"], p.target)
     for s in (s0, s1):
         x = s.solve(bt, check_status=True).cpu().numpy()
