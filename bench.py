@@ -283,6 +283,42 @@ def time_solves(torch, sysm, bt, xt, steps, warmup, flush, stream, label):
     return ms, wall
 
 
+def warm_times(torch, sysm, bt, xt, steps, stream):
+    sysm.solve(bt, xt)
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysm.solve(bt, xt)
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def level_handoffs(torch, sysm, bt, xt) -> dict:
+    """Per-level completion stamps (%globaltimer) of one solve: the time from one level's end
+    to the next, split by level width (thin <= 32 rows, the others)."""
+    st = torch.zeros(max(int(sysm.m), 1), dtype=torch.int64, device=bt.device)
+    sysm.solve(bt, xt, stamps=st)
+    torch.cuda.synchronize()
+    t = st.cpu().numpy()[:int(sysm.m)].astype(np.int64)
+    if t.size < 2:
+        return {}
+    width = np.bincount(sysm.export()["level"], minlength=int(sysm.m))
+    d = np.diff(t)
+    thin = width[1:] <= 32
+    out = {}
+    for name, sel in (("thin_levels", thin), ("wide_levels", ~thin)):
+        if sel.any():
+            v = d[sel]
+            out[name] = {"count": int(sel.sum()), "median_ns": float(np.median(v)), "p90_ns": float(np.percentile(v, 90)),
+                         "total_ms": round(float(v.sum()) / 1e6, 3)}
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -337,6 +373,11 @@ def run_ours(args):
         s.status()
     us_plain = statistics.mean(ms_plain) * 1e3
     us_rw = statistics.mean(ms_rw) * 1e3
+    med_rw = statistics.median(ms_rw) * 1e3
+    # warm: the same solves back to back, inputs left in L2 (outside the timed region of `value`)
+    warm_rw = statistics.median(warm_times(torch, rw, bt, xr, max(3, min(args.steps, 20)), stream)) * 1e3
+    warm_pl = statistics.median(warm_times(torch, plain, bt, xp, max(3, min(args.steps, 20)), stream)) * 1e3
+    hand = level_handoffs(torch, rw, bt, xr)
     # end to end through the public API: pinned host b -> device, solve, device -> host x
     hb = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
     hx = torch.empty_like(hb).pin_memory()
@@ -426,6 +467,9 @@ def run_ours(args):
             "autotune_ms": round(tune_ms, 1),
             "autotune_best": tuned,
             "rel_err_vs_x_true": errs,
+            "median_us": round(med_rw, 3),
+            "warm_us": {"rewritten": round(warm_rw, 3), "plain": round(warm_pl, 3)},
+            "level_handoffs": hand,
             "l2": "flushed (512 MB write) before every timed solve, outside the timed events",
             "parallelism": "replicas" if world > 1 else "1 GPU",
         },

@@ -143,9 +143,10 @@ typedef struct {
     int64_t max_spread;            /* per-row rule (Section III.A, the cache-locality constraint), > 0: a row moves
                                       only while max - min of its dependencies is below max_spread.  A row that breaks
                                       a rule stops its group like a cost overflow (its level becomes the next target). */
-    int32_t learned_mode;          /* LEARNED: 0 = the picker's plan and the naive plan are both built and timed
-                                      (one right-hand side), the faster is kept -- the paper's strategy is the
-                                      fallback and the measured solve time decides; 1 = the picker's plan only */
+    int32_t learned_mode;          /* LEARNED: 0 = the picker's plan, the naive plan and the plain (not rewritten)
+                                      system are built and timed (one right-hand side) and the fastest is kept --
+                                      the paper's strategy and no rewrite are the fallbacks, the measured solve time
+                                      decides; 1 = the picker's plan only */
 } sptrsv_strategy;
 
 /* Plans the rewrite with the strategy, rewrites the chosen rows (substitution of every
@@ -171,7 +172,7 @@ typedef struct {
     int32_t block;         /* solve schedule: block size, */
     int32_t run_width;     /*   widest level inside a single-CTA run (0 auto, -1 none, -2 one launch per level), */
     int32_t lanes_per_row; /*   lanes per row (0 auto) */
-    int32_t strategy_used; /* SPTRSV_STRATEGY_* that produced the stored plan (LEARNED resolves to CHOSEN or NAIVE) */
+    int32_t strategy_used; /* SPTRSV_STRATEGY_* of the stored plan (LEARNED resolves to CHOSEN, NAIVE or NONE) */
     int32_t launches;      /* kernels one single-RHS solve launches with the current schedule (0 before the
                               first solve or tune) */
 } sptrsv_system_info;

@@ -397,21 +397,28 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
         return rc;
     }
     naive->strategy_used = SPTRSV_STRATEGY_NAIVE;
-    double t_model = 0, t_naive = 0;
-    rc = time_solve_us(model, 5, &t_model, st);
-    if (rc == SPTRSV_OK) rc = time_solve_us(naive, 5, &t_naive, st);
+    // and not rewriting at all: the plain level-set system
+    sptrsv_system* plain = nullptr;
+    rc = sptrsv_system_plain(L, lvh, &plain, st);
     if (rc != SPTRSV_OK) {
         sptrsv_system_destroy(model);
         sptrsv_system_destroy(naive);
         return rc;
     }
-    if (t_model <= t_naive) {
-        sptrsv_system_destroy(naive);
-        *out = model;
-    } else {
-        sptrsv_system_destroy(model);
-        *out = naive;
+    plain->strategy_used = SPTRSV_STRATEGY_NONE;
+    sptrsv_system* cand[3] = {model, naive, plain};
+    double t[3] = {0, 0, 0};
+    for (int i = 0; i < 3 && rc == SPTRSV_OK; ++i) rc = time_solve_us(cand[i], 5, &t[i], st);
+    if (rc != SPTRSV_OK) {
+        for (sptrsv_system* c : cand) sptrsv_system_destroy(c);
+        return rc;
     }
+    int best = 0;
+    for (int i = 1; i < 3; ++i)
+        if (t[i] < t[best]) best = i;
+    for (int i = 0; i < 3; ++i)
+        if (i != best) sptrsv_system_destroy(cand[i]);
+    *out = cand[best];
     return SPTRSV_OK;
 }
 

@@ -43,13 +43,12 @@ __device__ bool wait_segment(const SolveArgs<T>& a, int s) {
     return !__syncthreads_or(failed);
 }
 
+// The barrier orders every thread's stores of the segment before thread 0's store; the
+// release (cumulative, gpu scope) makes them visible to whoever acquires the flag.
 template <typename T>
 __device__ __forceinline__ void publish(const SolveArgs<T>& a, int s) {
     __syncthreads();
-    if (threadIdx.x == 0 && s != a.withhold) {
-        __threadfence();
-        st_release(a.flags + blockIdx.x, s);
-    }
+    if (threadIdx.x == 0 && s != a.withhold) st_release(a.flags + blockIdx.x, s);
 }
 
 // b-part partial over this lane's share of the E row (lanes split the row)

@@ -44,7 +44,9 @@ def structure(sysm, lv_level) -> dict:
             "rows_rewritten": int(moved.sum())}
 
 
-def report(seed: int = 0, time_solves: bool = True, scale: float = 1.0) -> dict:
+def report(seed: int = 0, time_solves: bool = True, scale: float = 1.0, picker=None) -> dict:
+    """Structure (and solve time) of none / naive / manual -- and learned, when a trained
+    picker is given (nnz cap 1.5) -- on the lung2- and torso2-shaped inputs."""
     import torch
     out = {}
     for name, gen in (("lung2", S.gen_lung2_like), ("torso2", S.gen_torso2_like)):
@@ -54,7 +56,10 @@ def report(seed: int = 0, time_solves: bool = True, scale: float = 1.0) -> dict:
         level = lv.export()["level"]
         b = torch.from_numpy(S.rhs_from_xtrue(m, 1, 3)[1][0]).cuda()
         rows = {}
-        for strat, kw in (("none", {}), ("naive", dict(kind=B.NAIVE)), ("manual", dict(kind=B.MANUAL, k=9))):
+        strategies = [("none", {}), ("naive", dict(kind=B.NAIVE)), ("manual", dict(kind=B.MANUAL, k=9))]
+        if picker is not None:
+            strategies.append(("learned", dict(kind=B.LEARNED, cap=1.5, picker=picker)))
+        for strat, kw in strategies:
             s = B.System(M, lv, **kw)
             r = structure(s, level)
             if time_solves:
@@ -72,7 +77,7 @@ def report(seed: int = 0, time_solves: bool = True, scale: float = 1.0) -> dict:
                     ts.append(e0.elapsed_time(e1) * 1e3)
                 s.status()
                 r["solve_us"] = statistics.median(ts)
-            r["paper"] = PAPER[name][strat]
+            r["paper"] = PAPER[name].get(strat)
             rows[strat] = r
         out[name] = {"n": m.n, "nnz": m.nnz, "rows": rows}
     return out
@@ -84,17 +89,19 @@ def format_table(rep: dict) -> str:
     for name, d in rep.items():
         for strat, r in d["rows"].items():
             p = r["paper"]
+            ref = (f"{p['levels']} / {p['avg_cost']} / {p['total_cost']:,} / {p['rows_rewritten']:,}" if p
+                   else "not in the paper")
             lines.append(f"| {name} (n={d['n']:,}) | {strat} | {r['levels']} | {r['avg_cost']:.1f} | {r['total_cost']:,} | "
-                         f"{r['rows_rewritten']:,} | {r.get('solve_us', float('nan')):.1f} | "
-                         f"{p['levels']} / {p['avg_cost']} / {p['total_cost']:,} / {p['rows_rewritten']:,} |")
+                         f"{r['rows_rewritten']:,} | {r.get('solve_us', float('nan')):.1f} | {ref} |")
     return "\n".join(lines)
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--json", default=None)
+    ap.add_argument("--picker", default=None, help="trained picker file: adds the learned strategy")
     a = ap.parse_args(argv)
-    rep = report()
+    rep = report(picker=B.Picker.load(a.picker) if a.picker else None)
     print(format_table(rep))
     if a.json:
         json.dump(rep, open(a.json, "w"), indent=1)
