@@ -81,6 +81,9 @@ std::map<std::vector<int64_t>, Tuned> g_tune_cache;
 
 int lanes_for(int nrhs, double avg_row, int mode) {
     int lpr;
+    // mode 3: lanes per row split only the coefficients; thin levels of several right-hand
+    // sides then run in the fast executor (one lane per row and right-hand side)
+    if (mode == 3) return avg_row > 12.0 ? 4 : 1;
     if (nrhs >= 2) {
         lpr = 1;
         while (lpr < nrhs && lpr < 32) lpr <<= 1;
@@ -293,7 +296,7 @@ sptrsv_status sptrsv_batch_create(const sptrsv_system* const* systems, const int
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int mode = 0; mode < 3; ++mode) {
+            for (int mode = 0; mode < 4; ++mode) {
                 if ((rc = layout_batch(bt, mode)) != SPTRSV_OK) return fail(rc);
                 for (int block : {128, 256, 512}) {
                     float best_ms = 1e30f;

@@ -14,8 +14,8 @@
 //   write-out: the block's x leaves the ring once, coalesced.
 //
 // Fast blocks.  An SM runs at most four float64 warp instructions at a time, each for ~64
-// cycles, and a predicated-off one still takes its slot.  A fast block (one right-hand
-// side, every level within 32 lanes, at most K_MAX FMAs per lane) therefore runs exactly K
+// cycles, and a predicated-off one still takes its slot.  A fast block (every level within
+// 32 lanes of rows x right-hand sides x lanes per row, at most K_MAX FMAs per lane) runs exactly K
 // FMAs per lane and level, K fixed for the block: the staging pads each lane to K records
 // {coefficient, ring slot} with {0, zero slot}, and warp 0 runs a branch-free loop whose
 // per-level metadata is loaded one level ahead.
@@ -88,9 +88,11 @@ inline size_t run_stage_bytes(int vb, int nrhs, const RunGeom& g) {
     return (size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) + (size_t)(3 * g.stage_rows + 2) * 4;
 }
 
-// the ring holds ring_rows x nrhs values plus RING_PAD spare values: the zero slot (read by
-// the padding records of fast blocks, always 0) and the dummy slot (written by their idle lanes)
-constexpr int RING_PAD = 4;
+// the ring holds ring_rows x nrhs values plus RING_PAD spare values: two extra slots (rows) of
+// nrhs <= 32 values each -- the zero slot ring_rows (read by the padding records of fast
+// blocks, always 0) and the dummy slot ring_rows + 1 (written by their idle lanes)
+constexpr int RING_PAD = 64;
+constexpr int FAST_MAX_RHS = RING_PAD / 2;
 
 // the x ring plus two staging buffers (one is filled while the other is computed)
 inline size_t run_smem_bytes(int vb, int nrhs, const RunGeom& g) {
@@ -128,14 +130,14 @@ struct RunSmem {
     int32_t* row;
     int32_t* lp;
     RunGeom g;
-    int zero_slot;    // ring index that always holds 0
-    int dummy_slot;   // ring index that idle lanes write
+    int zero_slot;    // ring slot (row) whose nrhs values are always 0
+    int dummy_slot;   // ring slot (row) that idle lanes write
     // buffer 0 or 1 of the staging area; the ring is shared
     __device__ void carve(unsigned char* base, int nrhs, RunGeom geo, int buf = 0) {
         g = geo;
         ring = (T*)base;
-        zero_slot = g.ring_rows * nrhs;
-        dummy_slot = zero_slot + 1;
+        zero_slot = g.ring_rows;
+        dummy_slot = g.ring_rows + 1;
         const size_t vb = sizeof(T);
         const size_t stage = ((size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) +
                               (size_t)(3 * g.stage_rows + 2) * 4 + 15) / 16 * 16;
@@ -183,27 +185,27 @@ __device__ void run_stage_a(const SysView<T>& v, RunSmem<T>& sm, int l0, int nl,
         q = q < P0 ? P0 : (q > P1 ? P1 : q);
         sm.lp[li] = (int32_t)(q - P0);
     }
-    for (int i = G.tid; i < rows; i += G.nthr) {
+    // a thread per (row, right-hand side): b-part t = i * nrhs + k
+    for (int t = G.tid; t < rows * nrhs; t += G.nthr) {
+        const int i = t / nrhs, k = t - i * nrhs;
         const int64_t p = P0 + i;
         const int32_t row = v.perm[p];
-        sm.row[i] = row;
-        if (v.bpre) {
-            for (int k = 0; k < nrhs; ++k) sm.bp[(size_t)i * nrhs + k] = __ldcg(v.bpre + p * nrhs + k);
-        } else {
-            for (int k = 0; k < nrhs; ++k) sm.bp[(size_t)i * nrhs + k] = bpart_full(v, p, row, k);
-        }
+        if (k == 0) sm.row[i] = row;
+        sm.bp[t] = v.bpre ? __ldcg(v.bpre + p * nrhs + k) : bpart_full(v, p, row, k);
     }
 }
 
 // stage B: fold coefficients of dependencies older than the ring window into the
-// b-part; compact the others with their ring slots.  Same thread-to-row mapping as
-// stage A, so the b-part needs no barrier in between.
+// b-part; compact the others with their ring slots.  The folding uses stage A's mapping of
+// threads to b-parts (row with one right-hand side, (row, right-hand side) with several), so
+// the b-parts need no barrier in between.
 template <typename T>
 __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int rows, int64_t ring_lo,
                                  const Grp& G, int nl, int K, int lpr) {
     const int mask = sm.g.ring_rows - 1;
+    const int nrhs = v.nrhs;
     const int steps = K * lpr;  // records per row
-    G.sync();                   // the level pointers of stage A, written by other threads
+    G.sync();                   // the level pointers and b-parts of stage A, written by other threads
     for (int i = G.tid; i < rows; i += G.nthr) {
         // level of row i: the last li with lp[li] <= i
         int lo = 0, hi = nl - 1;
@@ -220,7 +222,7 @@ __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0
         const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
         // a fast row has at most K * lpr entries: its loads go out QC at a time
         constexpr int QC = 8;
-        T bp = sm.bp[i];
+        T bp = sm.bp[(size_t)i * nrhs];
         int j = 0;
         for (int qb = q0; qb < q1; qb += QC) {
             int32_t dd[QC];
@@ -243,7 +245,7 @@ __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0
                     }
                     ++j;
                 } else {
-                    bp -= cc[u] * __ldcg(v.xp + d);
+                    bp -= cc[u] * __ldcg(v.xp + (int64_t)d * nrhs);
                 }
             }
         }
@@ -252,7 +254,24 @@ __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0
             e.cv = T(0);
             e.slot = sm.zero_slot;
         }
-        sm.bp[i] = bp;
+        sm.bp[(size_t)i * nrhs] = bp;
+    }
+    if (nrhs > 1) {
+        // the other right-hand sides of the folded dependencies, a thread per (row, right-hand
+        // side); the first one (k = 0) was folded above by the thread of the row
+        G.sync();
+        for (int t = G.tid; t < rows * nrhs; t += G.nthr) {
+            const int i = t / nrhs, k = t - i * nrhs;
+            if (k == 0) continue;
+            const int64_t p = P0 + i;
+            const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
+            T acc = sm.bp[t];
+            for (int q = q0; q < q1; ++q) {
+                const int32_t d = v.ccol[q];
+                if (d < ring_lo) acc -= v.cval[q] * __ldcg(v.xp + (int64_t)d * nrhs + k);
+            }
+            sm.bp[t] = acc;
+        }
     }
     G.sync();
 }
@@ -266,21 +285,39 @@ __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int
     }
     const int nrhs = v.nrhs;
     const int mask = sm.g.ring_rows - 1;
-    for (int i = G.tid; i < rows; i += G.nthr) {
-        const int64_t p = P0 + i;
-        const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
-        int near = 0;
-        for (int q = q0; q < q1; ++q) {
-            const int32_t d = v.ccol[q];
-            if (d >= ring_lo) {
-                ++near;
-            } else {
-                const T c = v.cval[q];
-                for (int k = 0; k < nrhs; ++k)
-                    sm.bp[(size_t)i * nrhs + k] -= c * __ldcg(v.xp + (int64_t)d * nrhs + k);
+    if (nrhs == 1) {
+        for (int i = G.tid; i < rows; i += G.nthr) {
+            const int64_t p = P0 + i;
+            const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
+            int near = 0;
+            for (int q = q0; q < q1; ++q) {
+                const int32_t d = v.ccol[q];
+                if (d >= ring_lo) ++near;
+                else sm.bp[i] -= v.cval[q] * __ldcg(v.xp + d);
             }
+            sm.cptr[i + 1] = near;
         }
-        sm.cptr[i + 1] = near;
+    } else {
+        // near counts a thread per row; the folding a thread per (row, right-hand side), the
+        // mapping of stage A, so that neighbouring lanes read neighbouring values of x
+        for (int i = G.tid; i < rows; i += G.nthr) {
+            const int64_t p = P0 + i;
+            const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
+            int near = 0;
+            for (int q = q0; q < q1; ++q) near += v.ccol[q] >= ring_lo;
+            sm.cptr[i + 1] = near;
+        }
+        for (int t = G.tid; t < rows * nrhs; t += G.nthr) {
+            const int i = t / nrhs, k = t - i * nrhs;
+            const int64_t p = P0 + i;
+            const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
+            T acc = sm.bp[t];
+            for (int q = q0; q < q1; ++q) {
+                const int32_t d = v.ccol[q];
+                if (d < ring_lo) acc -= v.cval[q] * __ldcg(v.xp + (int64_t)d * nrhs + k);
+            }
+            sm.bp[t] = acc;
+        }
     }
     G.sync();
     // inclusive scan of the near counts by the group's first warp
@@ -317,30 +354,39 @@ __device__ void run_stage_b(const SysView<T>& v, RunSmem<T>& sm, int64_t P0, int
     G.sync();
 }
 
-// Fast block compute, warp 0.  Lane (g * LPR + e) of a level takes row g of the level and
-// its FMA steps e, e + LPR, ...: K records, its row's b-part on e = 0, the ring load of each
-// dependency, K float64 FMAs, log2(LPR) shuffle adds, one store.  The records of level li + 1
-// are loaded while level li computes (two register sets, alternating), and the level pointers
-// two levels ahead.
-template <typename T, int K>
+// Fast block compute, warp 0.  Lane ((g * R2 + k) * LPR + e) of a level takes row g of the
+// level, right-hand side k (R2: nrhs rounded up to a power of two) and the row's FMA steps
+// e, e + LPR, ...: K records (shared by the row's right-hand sides), its row's b-part on e = 0,
+// the ring load of each dependency, K float64 FMAs, log2(LPR) shuffle adds, one store.  The
+// records of level li + 1 are loaded while level li computes (two register sets, alternating),
+// and the level pointers two levels ahead.
+template <typename T, int K, int RPL>
 struct FastOps {
-    int slot[K];
+    int slot[K];  // ring slot (row) of each step's dependency
     T cv[K];
-    T bp;
-    int out;
+    T bp[RPL];
+    int out[RPL];  // ring elements the lane writes
 };
 
-template <typename T, int LPR, int K>
-__device__ __forceinline__ void fast_load(const RunSmem<T>& sm, int64_t P0, int mask, int lb, int le,
-                                          FastOps<T, K>& o) {
-    const int lane = (int)threadIdx.x;
-    const int nlanes = (le - lb) * LPR;
-    const bool act = lane < nlanes;
-    const FastRec<T>* r = sm.rec + (size_t)K * LPR * lb + lane;
+struct FastLane {
+    int g, k, e, nrhs;  // row in the level, first right-hand side, coefficient lane
+    int lanes;          // lanes per row: LPR x (right-hand sides rounded up to a power of two) / RPL
+};
+
+// MR: several right-hand sides, RPL of them per lane (lane = (g * r2 / RPL + k / RPL) * LPR + e);
+// otherwise one (lane = g * LPR + e)
+template <typename T, int LPR, int K, bool MR, int RPL>
+__device__ __forceinline__ void fast_load(const RunSmem<T>& sm, const FastLane& fl, int64_t P0, int mask, int lb,
+                                          int le, FastOps<T, K, RPL>& o) {
+    const int nr = MR ? fl.nrhs : 1;
+    const int rows = le - lb;
+    const int nrec = rows * LPR;  // record lanes of the level (one per row and coefficient lane)
+    const bool act = fl.g < rows && (!MR || fl.k < fl.nrhs);
+    const FastRec<T>* r = sm.rec + (size_t)K * LPR * lb + fl.g * LPR + fl.e;
 #pragma unroll
     for (int u = 0; u < K; ++u) {
         if (act) {
-            const FastRec<T> e = r[u * nlanes];
+            const FastRec<T> e = r[u * nrec];
             o.slot[u] = e.slot;
             o.cv[u] = e.cv;
         } else {
@@ -348,65 +394,102 @@ __device__ __forceinline__ void fast_load(const RunSmem<T>& sm, int64_t P0, int 
             o.cv[u] = T(0);
         }
     }
-    const int i = lb + lane / LPR;
-    const bool head = act && (lane & (LPR - 1)) == 0;
-    o.bp = head ? sm.bp[i] : T(0);
-    o.out = head ? (int)((P0 + i) & mask) : sm.dummy_slot;
+    const int i = lb + fl.g;
+    const bool head = act && fl.e == 0;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int k = MR ? fl.k + j : 0;
+        const bool hj = head && k < nr;
+        o.bp[j] = hj ? sm.bp[(size_t)i * nr + k] : T(0);
+        o.out[j] = hj ? (int)((P0 + i) & mask) * nr + k : sm.dummy_slot * nr + j;
+    }
 }
 
-template <typename T, int LPR, int K>
-__device__ __forceinline__ void fast_level(RunSmem<T>& sm, const FastOps<T, K>& o) {
-    T xv[K];
+template <typename T, int LPR, int K, bool MR, int RPL>
+__device__ __forceinline__ void fast_level(RunSmem<T>& sm, const FastLane& fl, const FastOps<T, K, RPL>& o) {
+    const int nr = MR ? fl.nrhs : 1;
+    T acc[RPL];
 #pragma unroll
-    for (int u = 0; u < K; ++u) xv[u] = sm.ring[o.slot[u]];
-    T acc = o.bp;
+    for (int j = 0; j < RPL; ++j) {
+        // a right-hand side past nrhs reads the zero slot's values (its k stays below 32)
+        const int k = MR ? min(fl.k + j, fl.nrhs - 1) : 0;
+        T xv[K];
 #pragma unroll
-    for (int u = 0; u < K; ++u) acc -= o.cv[u] * xv[u];
+        for (int u = 0; u < K; ++u) xv[u] = sm.ring[o.slot[u] * nr + k];
+        acc[j] = o.bp[j];
 #pragma unroll
-    for (int sh = 1; sh < LPR; sh <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sh);
-    sm.ring[o.out] = acc;
+        for (int u = 0; u < K; ++u) acc[j] -= o.cv[u] * xv[u];
+    }
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+#pragma unroll
+        for (int sh = 1; sh < LPR; sh <<= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], sh);
+        sm.ring[o.out[j]] = acc[j];
+    }
     __syncwarp();
 }
 
-template <typename T, int LPR, int K>
-__device__ void run_compute_fast(RunSmem<T>& sm, int64_t P0, int l0, int nl, unsigned long long* stamps) {
+template <typename T, int LPR, int K, bool MR, int RPL>
+__device__ void run_compute_fast(RunSmem<T>& sm, int nrhs, int64_t P0, int l0, int nl, unsigned long long* stamps) {
     if (threadIdx.x >= 32) return;
     const int mask = sm.g.ring_rows - 1;
+    FastLane fl;
+    fl.nrhs = nrhs;
+    int r2 = 1;
+    if (MR)
+        while (r2 < nrhs) r2 <<= 1;
+    const int kl = MR ? r2 / RPL : 1;  // lanes of a row's right-hand sides
+    fl.e = (int)threadIdx.x & (LPR - 1);
+    fl.k = MR ? (((int)threadIdx.x / LPR) % kl) * RPL : 0;
+    fl.g = (int)threadIdx.x / (LPR * kl);
+    fl.lanes = LPR * kl;
     auto lpb = [&](int li) { return li < nl ? sm.lp[li] : 0; };
     auto lpe = [&](int li) { return li < nl ? sm.lp[li + 1] : 0; };
-    FastOps<T, K> oa, ob;
+    FastOps<T, K, RPL> oa, ob;
     int b1 = lpb(1), e1 = lpe(1), b2 = lpb(2), e2 = lpe(2);
-    fast_load<T, LPR, K>(sm, P0, mask, lpb(0), lpe(0), oa);
+    fast_load<T, LPR, K, MR, RPL>(sm, fl, P0, mask, lpb(0), lpe(0), oa);
     for (int li = 0; li < nl; li += 2) {
         const int b3 = lpb(li + 3), e3 = lpe(li + 3);
-        fast_load<T, LPR, K>(sm, P0, mask, b1, e1, ob);
-        fast_level<T, LPR, K>(sm, oa);
+        fast_load<T, LPR, K, MR, RPL>(sm, fl, P0, mask, b1, e1, ob);
+        fast_level<T, LPR, K, MR, RPL>(sm, fl, oa);
         if (stamps && threadIdx.x == 0) stamps[l0 + li] = globaltimer();
         if (li + 1 >= nl) break;
         const int b4 = lpb(li + 4), e4 = lpe(li + 4);
-        fast_load<T, LPR, K>(sm, P0, mask, b2, e2, oa);
-        fast_level<T, LPR, K>(sm, ob);
+        fast_load<T, LPR, K, MR, RPL>(sm, fl, P0, mask, b2, e2, oa);
+        fast_level<T, LPR, K, MR, RPL>(sm, fl, ob);
         if (stamps && threadIdx.x == 0) stamps[l0 + li + 1] = globaltimer();
         b1 = b3; e1 = e3; b2 = b4; e2 = e4;
     }
 }
 
-template <typename T, int LPR>
-__device__ void run_compute_fast_k(RunSmem<T>& sm, int K, int64_t P0, int l0, int nl, unsigned long long* stamps) {
+template <typename T, int LPR, bool MR, int RPL>
+__device__ void run_compute_fast_k(RunSmem<T>& sm, int nrhs, int K, int64_t P0, int l0, int nl,
+                                   unsigned long long* stamps) {
     switch (K) {
-        case 1: run_compute_fast<T, LPR, 1>(sm, P0, l0, nl, stamps); break;
-        case 2: run_compute_fast<T, LPR, 2>(sm, P0, l0, nl, stamps); break;
-        case 3: run_compute_fast<T, LPR, 3>(sm, P0, l0, nl, stamps); break;
-        default: run_compute_fast<T, LPR, 4>(sm, P0, l0, nl, stamps); break;
+        case 1: run_compute_fast<T, LPR, 1, MR, RPL>(sm, nrhs, P0, l0, nl, stamps); break;
+        case 2: run_compute_fast<T, LPR, 2, MR, RPL>(sm, nrhs, P0, l0, nl, stamps); break;
+        case 3: run_compute_fast<T, LPR, 3, MR, RPL>(sm, nrhs, P0, l0, nl, stamps); break;
+        default: run_compute_fast<T, LPR, 4, MR, RPL>(sm, nrhs, P0, l0, nl, stamps); break;
     }
 }
 
+// right-hand sides per lane of a fast block: one up to 16, two above
+__host__ __device__ inline int fast_rhs_per_lane(int nrhs) { return nrhs > 16 ? 2 : 1; }
+
 template <typename T>
-__device__ void run_compute_fast_any(RunSmem<T>& sm, int lpr, int K, int64_t P0, int l0, int nl,
+__device__ void run_compute_fast_any(RunSmem<T>& sm, int lpr, int nrhs, int K, int64_t P0, int l0, int nl,
                                      unsigned long long* stamps) {
-    if (lpr == 1) run_compute_fast_k<T, 1>(sm, K, P0, l0, nl, stamps);
-    else if (lpr == 2) run_compute_fast_k<T, 2>(sm, K, P0, l0, nl, stamps);
-    else run_compute_fast_k<T, 4>(sm, K, P0, l0, nl, stamps);
+    if (nrhs == 1) {
+        if (lpr == 1) run_compute_fast_k<T, 1, false, 1>(sm, 1, K, P0, l0, nl, stamps);
+        else if (lpr == 2) run_compute_fast_k<T, 2, false, 1>(sm, 1, K, P0, l0, nl, stamps);
+        else run_compute_fast_k<T, 4, false, 1>(sm, 1, K, P0, l0, nl, stamps);
+    } else if (fast_rhs_per_lane(nrhs) == 1) {
+        if (lpr == 1) run_compute_fast_k<T, 1, true, 1>(sm, nrhs, K, P0, l0, nl, stamps);
+        else run_compute_fast_k<T, 2, true, 1>(sm, nrhs, K, P0, l0, nl, stamps);
+    } else {
+        if (lpr == 1) run_compute_fast_k<T, 1, true, 2>(sm, nrhs, K, P0, l0, nl, stamps);
+        else run_compute_fast_k<T, 2, true, 2>(sm, nrhs, K, P0, l0, nl, stamps);
+    }
 }
 
 // the level loop of one staged block; narrow blocks run on warp 0 alone
@@ -472,7 +555,7 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
     {
         RunSmem<T> s0;
         s0.carve(smem, v.nrhs, geo, 0);
-        if (threadIdx.x < RING_PAD) s0.ring[s0.zero_slot + threadIdx.x] = T(0);
+        if (threadIdx.x < RING_PAD) s0.ring[(size_t)s0.zero_slot * v.nrhs + threadIdx.x] = T(0);
         const int4 bd = blocks[blk0];
         __syncthreads();
         run_stage_a(v, s0, bd.z, bd.w & BLK_NL_MASK, bd.x, bd.y, grp_all());
@@ -495,7 +578,7 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
         const bool overlap = fast && blockDim.x > 32 && (prev || next);
         if (overlap) {
             if (threadIdx.x < 32) {
-                run_compute_fast_any(cur, ln.lpr, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
+                run_compute_fast_any(cur, ln.lpr, v.nrhs, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
             } else {
                 const Grp G = grp_stagers();
                 if (prev) {
@@ -516,7 +599,8 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
                 run_write_out(v, oth, bp.x, (int)(bp.y - bp.x), grp_all());
             }
             if (fast) {
-                if (threadIdx.x < 32) run_compute_fast_any(cur, ln.lpr, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
+                if (threadIdx.x < 32)
+                    run_compute_fast_any(cur, ln.lpr, v.nrhs, (bd.w >> BLK_K_SHIFT) & 7, P0, bd.z, nl, stamps);
             } else {
                 run_compute(v, cur, ln, narrow, P0, bd.z, nl, stamps);
             }
@@ -540,9 +624,10 @@ __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo
     return true;
 }
 
-// host: cuts levels [l_begin, l_end) into staged blocks; levels that qualify (one
-// right-hand side, lpr 1, 2 or 4, at most 32 lanes, at most K_MAX FMA steps per lane) go to
-// fast blocks of at most fast_recs records (0: no fast blocks)
+// host: cuts levels [l_begin, l_end) into staged blocks; levels that qualify (lpr 1, 2 or 4 for
+// one right-hand side, 1 or 2 for several; rows x lpr x nrhs rounded up to a power of two /
+// right-hand sides per lane at most 32 lanes; at most K_MAX FMA steps per lane) go to fast
+// blocks of at most fast_recs records (0: no fast blocks)
 int build_run_blocks(const int32_t* lp, const int32_t* cptr, int64_t l_begin, int64_t l_end, int stage_rows,
                      int stage_entries, int lpr, int nrhs, int fast_recs, std::vector<int4>& out);
 

@@ -98,12 +98,16 @@ int pow2_floor(int64_t v) {
 // coefficients than the staging area holds.
 int build_run_blocks(const int32_t* lp, const int32_t* cptr, int64_t l_begin, int64_t l_end, int stage_rows,
                      int stage_entries, int lpr, int nrhs, int fast_recs, std::vector<int4>& out) {
-    const bool fast_on = fast_recs > 0 && nrhs == 1 && (lpr == 1 || lpr == 2 || lpr == 4);
+    const bool fast_on = fast_recs > 0 && nrhs <= FAST_MAX_RHS &&
+                         (lpr == 1 || lpr == 2 || (lpr == 4 && nrhs == 1));
+    int r2 = 1;  // right-hand sides rounded up to a power of two
+    while (r2 < nrhs) r2 <<= 1;
+    r2 /= fast_rhs_per_lane(nrhs);  // lanes of a row's right-hand sides
     // FMA steps a level needs in a fast block, or 0 when the level does not qualify
     auto fast_k = [&](int64_t l) -> int {
         if (!fast_on) return 0;
         const int64_t rows = lp[l + 1] - lp[l];
-        if (rows * lpr > 32) return 0;
+        if (rows * lpr * r2 > 32) return 0;
         int64_t mx = 0;
         for (int64_t i = lp[l]; i < lp[l + 1]; ++i) mx = std::max<int64_t>(mx, (int64_t)cptr[i + 1] - cptr[i]);
         const int64_t k = std::max<int64_t>(1, (mx + lpr - 1) / lpr);
@@ -362,6 +366,8 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         int p = 1;
         while (p < nrhs && p < 32) p <<= 1;
         lprs = {std::max(1, p / 2), p};
+        // one lane per row and right-hand side: thin levels run in the fast executor
+        if (nrhs <= FAST_MAX_RHS && p / 2 > 1) lprs.push_back(1);
     }
     std::vector<int> widths = {0, 64, -1};
     if (s->m <= 256) widths.push_back(-2);  // one launch per level

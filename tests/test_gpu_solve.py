@@ -100,6 +100,24 @@ def test_plain_solve_schedule_variants(run_width, lpr):
     solve_and_compare(m, b, TOL_F64, tune=dict(run_width=run_width, lanes_per_row=lpr))
 
 
+@pytest.mark.parametrize("nrhs", [2, 5, 16, 32])
+@pytest.mark.parametrize("lpr", [1, 2])
+@pytest.mark.parametrize("f32", [False, True])
+def test_fast_thin_levels_several_rhs(nrhs, lpr, f32):
+    """Thin levels with several right-hand sides in the fast executor (one lane per row,
+    right-hand side and coefficient lane), plain and rewritten, against the oracle; the
+    dependencies older than the ring window are folded for every right-hand side."""
+    m = S.gen_skewed(30000, 8, head=12000)
+    if f32:
+        m = m.astype(np.float32)
+    b = S.rhs_uniform(m.n, nrhs, 9)
+    if f32:
+        b = b.astype(np.float32)
+    tol = TOL_F32 if f32 else TOL_F64
+    for kw in ({}, dict(kind=B.NAIVE, cap=1.5), dict(kind=B.DEPTH_K, k=3)):
+        solve_and_compare(m, b, tol, system_kw=kw, tune=dict(lanes_per_row=lpr))
+
+
 def test_plain_solve_float32_values():
     m = S.gen_banded_random(4000, 9).astype(np.float32)
     b = S.rhs_uniform(m.n, 3, 1).astype(np.float32)
