@@ -25,7 +25,7 @@ _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NAIVE, DEPTH, CHOSEN, MANUAL, CHOSEN_THIN = 1, 2, 3, 4, 5
+NAIVE, DEPTH, CHOSEN, MANUAL, CHOSEN_THIN, ROWCAP = 1, 2, 3, 4, 5, 6
 
 
 def build(force: bool = False) -> str:
@@ -176,7 +176,7 @@ class Plan:
 
 def plan(rowptr, colidx, level, m, kind: int, k: int = 0, avg: float = 0.0, cap: float = 0.0,
          injected_cost=None, depth_of_target=None, alpha: int = 0, beta: int = 0) -> Plan:
-    """The Section III planner (NAIVE / DEPTH / CHOSEN / MANUAL / CHOSEN_THIN), with the per-row rules of
+    """The Section III planner (NAIVE / DEPTH / CHOSEN / MANUAL / CHOSEN_THIN / ROWCAP), with the per-row rules of
     Section III.A (alpha: fewer dependencies than alpha; beta: dependency spread below beta)."""
     rp, ci, lv = _i32(rowptr), _i32(colidx), _i32(level)
     n = rp.size - 1

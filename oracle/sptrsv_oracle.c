@@ -172,6 +172,8 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
                          applied to the levels cheaper than avgLevelCost (Section IV) */
 #define ORC_CHOSEN_THIN 5  /* per-target depth over thin levels only: the learned picker's
                               depth choice within the thin-level rule of Section III */
+#define ORC_ROWCAP 6  /* thin levels, rows moved into a target while it holds at most k rows:
+                         the Section III walk with a row count in place of avgLevelCost */
 
 /*
  * Walk the levels in order and decide, row by row, the level each row moves to.
@@ -201,6 +203,10 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
  *   DEPTH (no cost rule).
  * CHOSEN_THIN: thin levels are eligible as in NAIVE, levels join a target by its own
  *   distance depth_of_target[t] as in CHOSEN (no cost rule).
+ * ROWCAP: NAIVE with the number of rows on the target in place of the cost: thin levels are
+ *   eligible, rows of the following thin levels move while the target holds fewer than k
+ *   rows; the first row that does not fit (or breaks the cap or a per-row rule) makes its
+ *   own level the new target, holding its remaining rows.
  *
  * inputs : lower-triangular CSR (diagonal last), level[n], m, kind, k, avg_override
  *          (<= 0: computed), cap_ratio (<= 0: no cap), injected_cost (NULL: computed),
@@ -273,9 +279,10 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
     int32_t t = -1;
     int64_t cur = 0;
     for (int32_t s = 0; s < m; ++s) {
-        int eligible = (kind == ORC_NAIVE || kind == ORC_MANUAL || kind == ORC_CHOSEN_THIN) ? ((double)lcost[s] < avg) : 1;
+        int eligible = (kind == ORC_NAIVE || kind == ORC_MANUAL || kind == ORC_CHOSEN_THIN || kind == ORC_ROWCAP)
+                           ? ((double)lcost[s] < avg) : 1;
         if (!eligible) { t = -1; continue; }
-        if (t < 0) { t = s; cur = lcost[s]; targets++; continue; }
+        if (t < 0) { t = s; cur = kind == ORC_ROWCAP ? (int64_t)(lptr[s + 1] - lptr[s]) : lcost[s]; targets++; continue; }
         if ((kind == ORC_DEPTH || kind == ORC_MANUAL) && s - t > k) { t = s; cur = lcost[s]; targets++; continue; }
         if ((kind == ORC_CHOSEN || kind == ORC_CHOSEN_THIN) && s - t > depth_of_target[t]) {
             t = s; cur = lcost[s]; targets++; continue;
@@ -305,7 +312,7 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
             }
             int64_t c = injected_cost ? injected_cost[r] : 2 * (int64_t)Dn.len;
             int64_t growth = (int64_t)Dn.len + (int64_t)En.len - (int64_t)D[r].len;
-            int fits_cost = (kind == ORC_NAIVE) ? ((double)(cur + c) <= avg) : 1;
+            int fits_cost = (kind == ORC_NAIVE) ? ((double)(cur + c) <= avg) : (kind == ORC_ROWCAP) ? (cur + 1 <= k) : 1;
             int fits_cap = (stored + growth <= limit);
             int fits_rules = 1;
             if (alpha > 0 && Dn.len >= alpha) fits_rules = 0;
@@ -314,7 +321,7 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
                 target[r] = t;
                 curlev[r] = t;
                 row_cost[r] = c;
-                cur += c;
+                cur += kind == ORC_ROWCAP ? 1 : c;
                 stored += growth;
                 moved++;
                 iset tmp = D[r]; D[r] = Dn; Dn = tmp;
@@ -326,7 +333,7 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
                 cur = 0;
                 for (int64_t q2 = lptr[s]; q2 < lptr[s + 1]; ++q2) {
                     int64_t r2 = byl[q2];
-                    if (curlev[r2] == s) cur += row_cost[r2];
+                    if (curlev[r2] == s) cur += kind == ORC_ROWCAP ? 1 : row_cost[r2];
                 }
                 break;
             }

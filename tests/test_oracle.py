@@ -442,6 +442,30 @@ def test_planner_chosen_thin_follows_per_target_depths_on_thin_levels():
         assert np.array_equal(p1.target, p2.target) and p1.moved == p2.moved > 0
 
 
+def test_planner_rowcap_counts_rows_on_thin_levels():
+    """ROWCAP: the Section III walk with a row count in place of avgLevelCost.  On a chain of
+    one-row thin levels a target of k rows takes the next k-1 levels (the MANUAL plan with
+    k-1); on general inputs no target ends with more than k rows, fat levels keep theirs."""
+    n = 300
+    chain = S.gen_from_deps(n, np.array([0] + [1] * (n - 1)), np.arange(n - 1), S.rng_for(6))
+    lev, mm = O.levels(chain.rowptr, chain.colidx)
+    for k in (2, 7, 16):
+        p1 = O.plan(chain.rowptr, chain.colidx, lev, mm, O.ROWCAP, k=k, avg=100.0)
+        p2 = O.plan(chain.rowptr, chain.colidx, lev, mm, O.MANUAL, k=k - 1, avg=100.0)
+        assert np.array_equal(p1.target, p2.target)
+    for m in (S.gen_torso2_like(scale=0.25), S.gen_config("c0")[0], S.gen_skewed(20000, 3, head=10000)):
+        lev, mm = O.levels(m.rowptr, m.colidx)
+        st = O.level_stats(m.rowptr, lev, mm)
+        for k in (8, 32):
+            p = O.plan(m.rowptr, m.colidx, lev, mm, O.ROWCAP, k=k, cap=1.5)
+            moved = p.target != lev
+            assert moved.any()
+            got = np.bincount(p.target, minlength=mm)
+            assert got[np.unique(p.target[moved])].max() <= k
+            fat = st["cost"] >= p.avg
+            assert np.all(p.target[fat[lev]] == lev[fat[lev]])
+
+
 @pytest.mark.parametrize("alpha,beta", [(3, 0), (0, 40), (4, 100), (1, 0)])
 def test_planner_per_row_rules(alpha, beta):
     """Section III.A rules: every rewritten row keeps fewer than alpha dependencies and a
