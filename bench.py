@@ -153,7 +153,7 @@ def chain_floor(sysm, sm_mhz: float) -> dict:
             "sm_mhz": sm_mhz, "floor_us": round(us, 1)}
 
 
-STRATEGY_NAMES = {0: "none", 1: "naive", 2: "depth_k", 3: "learned", 4: "chosen depths", 5: "manual"}
+STRATEGY_NAMES = {0: "none", 1: "naive", 2: "depth_k", 3: "learned", 4: "chosen depths", 5: "manual", 6: "rowcap"}
 
 
 def alg_bytes(info: dict, n: int, nrhs: int, v: int = 8) -> int:

@@ -122,8 +122,11 @@ enum {
     SPTRSV_STRATEGY_LEARNED = 3, /* thin levels (Section III) merged into targets at depths a trained picker
                                     chooses per target (NAIVE without a picker) */
     SPTRSV_STRATEGY_CHOSEN = 4,  /* depth per target given by the caller */
-    SPTRSV_STRATEGY_MANUAL = 5   /* fixed distance k over thin levels only: the manual approach of the earlier work
+    SPTRSV_STRATEGY_MANUAL = 5,  /* fixed distance k over thin levels only: the manual approach of the earlier work
                                     ("every 9 levels into the 10th", Sections III and IV) */
+    SPTRSV_STRATEGY_ROWCAP = 6   /* the Section III walk over thin levels with a row count in place of avgLevelCost:
+                                    a target takes rows while it holds at most k of them (k <= 0: 32, one warp's
+                                    lanes -- the width of a level in the fast thin-level executor) */
 };
 
 typedef struct {
@@ -143,10 +146,11 @@ typedef struct {
     int64_t max_spread;            /* per-row rule (Section III.A, the cache-locality constraint), > 0: a row moves
                                       only while max - min of its dependencies is below max_spread.  A row that breaks
                                       a rule stops its group like a cost overflow (its level becomes the next target). */
-    int32_t learned_mode;          /* LEARNED: 0 = the picker's plan, the naive plan and the plain (not rewritten)
-                                      system are built and timed (one right-hand side) and the fastest is kept --
-                                      the paper's strategy and no rewrite are the fallbacks, the measured solve time
-                                      decides; 1 = the picker's plan only */
+    int32_t learned_mode;          /* LEARNED: 0 = the picker's plan, the naive plan, the ROWCAP plan (32 rows) and
+                                      the plain (not rewritten) system are built and timed (one right-hand side)
+                                      and the fastest is kept -- the paper's strategy, the executor-shaped plan and
+                                      no rewrite are the fallbacks, the measured solve time decides; 1 = the
+                                      picker's plan only */
 } sptrsv_strategy;
 
 /* Plans the rewrite with the strategy, rewrites the chosen rows (substitution of every
@@ -172,9 +176,10 @@ typedef struct {
     int32_t block;         /* solve schedule: block size, */
     int32_t run_width;     /*   widest level inside a single-CTA run (0 auto, -1 none, -2 one launch per level), */
     int32_t lanes_per_row; /*   lanes per row (0 auto) */
-    int32_t strategy_used; /* SPTRSV_STRATEGY_* of the stored plan (LEARNED resolves to CHOSEN, NAIVE or NONE) */
+    int32_t strategy_used; /* SPTRSV_STRATEGY_* of the stored plan (LEARNED resolves to CHOSEN, NAIVE, ROWCAP or NONE) */
     int32_t launches;      /* kernels one single-RHS solve launches with the current schedule (0 before the
                               first solve or tune) */
+    int32_t ctas;          /* CTAs of the persistent solve kernel with the current schedule (SMs x CTAs per SM) */
 } sptrsv_system_info;
 
 sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsptrsv.so")
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNSUPPORTED"}
 F64, F32 = 0, 1
-NONE, NAIVE, DEPTH_K, LEARNED, CHOSEN, MANUAL = 0, 1, 2, 3, 4, 5
+NONE, NAIVE, DEPTH_K, LEARNED, CHOSEN, MANUAL, ROWCAP = 0, 1, 2, 3, 4, 5, 6
 PICKER_FEATURES, PICKER_HIDDEN = 12, 64
 PICKER_PARAMS = 12 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 
@@ -67,7 +67,7 @@ class SystemInfo(C.Structure):
                 ("segments", C.c_int64), ("run_levels", C.c_int64), ("dtype", C.c_int32),
                 ("rewritten", C.c_int32), ("avg_cost", C.c_double), ("block", C.c_int32),
                 ("run_width", C.c_int32), ("lanes_per_row", C.c_int32), ("strategy_used", C.c_int32),
-                ("launches", C.c_int32)]
+                ("launches", C.c_int32), ("ctas", C.c_int32)]
 
 
 class BatchInfo(C.Structure):

@@ -95,18 +95,7 @@ int lanes_for(int nrhs, double avg_row, int mode) {
     return lpr;
 }
 
-RunGeom geom_for(int nrhs, int vb) {
-    RunGeom g;
-    g.stage_entries = 1536;
-    g.stage_rows = (int)((32768 - (int64_t)g.stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
-    if (g.stage_rows < 16) {
-        g.stage_entries = 256;
-        g.stage_rows = (int)std::max<int64_t>(16, (32768 - (int64_t)g.stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
-    }
-    g.ring_rows = 16;
-    while (g.ring_rows < 2 * g.stage_rows) g.ring_rows *= 2;
-    return g;
-}
+RunGeom geom_for(int nrhs, int vb) { return run_geometry(nrhs, vb); }
 
 }  // namespace
 }  // namespace sp

@@ -116,6 +116,19 @@ __device__ __forceinline__ uint64_t globaltimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// Asks the TMA unit to bring [p, p + bytes) into L2 without waiting for it: the threads of
+// the CTA issue one bulk prefetch per 4 KB piece.  Only the 16-byte aligned interior of the
+// range is prefetched (the bulk copy's alignment rule), so nothing outside it is touched.
+__device__ __forceinline__ void l2_prefetch(const void* p, int64_t bytes) {
+    if (bytes <= 0) return;
+    constexpr uint64_t PIECE = 4096;
+    const uint64_t a = ((uint64_t)p + 15) & ~(uint64_t)15;
+    const uint64_t e = ((uint64_t)p + (uint64_t)bytes) & ~(uint64_t)15;
+    for (uint64_t q = a + (uint64_t)threadIdx.x * PIECE; q < e; q += (uint64_t)blockDim.x * PIECE) {
+        const uint32_t n = (uint32_t)(e - q < PIECE ? e - q : PIECE);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
+    }
+}
 #endif
 
 // status words written by kernels (device int, 0 = ok)

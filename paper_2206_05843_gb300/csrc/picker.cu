@@ -397,26 +397,38 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
         return rc;
     }
     naive->strategy_used = SPTRSV_STRATEGY_NAIVE;
+    // the plan shaped for the fast executor (targets of at most one warp's rows)
+    sptrsv_system* rowcap = nullptr;
+    rc = rewrite_system(L, lv, 6 /* rowcap */, ROWCAP_DEFAULT_ROWS, nullptr, sg->avg_override, sg->nnz_growth_cap,
+                        sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &rowcap, st);
+    if (rc != SPTRSV_OK) {
+        sptrsv_system_destroy(model);
+        sptrsv_system_destroy(naive);
+        return rc;
+    }
+    rowcap->strategy_used = SPTRSV_STRATEGY_ROWCAP;
     // and not rewriting at all: the plain level-set system
     sptrsv_system* plain = nullptr;
     rc = sptrsv_system_plain(L, lvh, &plain, st);
     if (rc != SPTRSV_OK) {
         sptrsv_system_destroy(model);
         sptrsv_system_destroy(naive);
+        sptrsv_system_destroy(rowcap);
         return rc;
     }
     plain->strategy_used = SPTRSV_STRATEGY_NONE;
-    sptrsv_system* cand[3] = {model, naive, plain};
-    double t[3] = {0, 0, 0};
-    for (int i = 0; i < 3 && rc == SPTRSV_OK; ++i) rc = time_solve_us(cand[i], 5, &t[i], st);
+    constexpr int NC = 4;
+    sptrsv_system* cand[NC] = {model, naive, rowcap, plain};
+    double t[NC] = {0, 0, 0, 0};
+    for (int i = 0; i < NC && rc == SPTRSV_OK; ++i) rc = time_solve_us(cand[i], 5, &t[i], st);
     if (rc != SPTRSV_OK) {
         for (sptrsv_system* c : cand) sptrsv_system_destroy(c);
         return rc;
     }
     int best = 0;
-    for (int i = 1; i < 3; ++i)
+    for (int i = 1; i < NC; ++i)
         if (t[i] < t[best]) best = i;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < NC; ++i)
         if (i != best) sptrsv_system_destroy(cand[i]);
     *out = cand[best];
     return SPTRSV_OK;

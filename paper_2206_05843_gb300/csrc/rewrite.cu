@@ -23,8 +23,10 @@ namespace sp {
 
 // kinds of the walk
 // CHOSEN_THIN: the learned strategy's plan -- thin levels only (Section III), each target
-// taking its own number of following levels
-enum { WALK_NAIVE = 1, WALK_DEPTH = 2, WALK_CHOSEN = 3, WALK_MANUAL = 4, WALK_CHOSEN_THIN = 5 };
+// taking its own number of following levels.  ROWCAP: the NAIVE walk with the number of rows on
+// the target (at most k) in place of avgLevelCost -- a level of the fast executor holds at
+// most 32 lanes, so the cap shapes the plan for it
+enum { WALK_NAIVE = 1, WALK_DEPTH = 2, WALK_CHOSEN = 3, WALK_MANUAL = 4, WALK_CHOSEN_THIN = 5, WALK_ROWCAP = 6 };
 
 namespace {
 
@@ -118,8 +120,11 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
     int64_t cur = 0, stored = a.nnzL, moved = 0, targets = 0, top = 0;
     for (int64_t s = 0; s < a.m; ++s) {
         const int64_t ls = a.lcost[s];
-        const bool eligible =
-            (a.kind == WALK_NAIVE || a.kind == WALK_MANUAL || a.kind == WALK_CHOSEN_THIN) ? ((double)ls < a.avg) : true;
+        const bool eligible = (a.kind == WALK_NAIVE || a.kind == WALK_MANUAL || a.kind == WALK_CHOSEN_THIN ||
+                               a.kind == WALK_ROWCAP)
+                                  ? ((double)ls < a.avg)
+                                  : true;
+        const bool rowcap = a.kind == WALK_ROWCAP;
         if (!eligible) {
             t = -1;
             continue;
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
         if (t < 0 || ((a.kind == WALK_DEPTH || a.kind == WALK_MANUAL) && s - t > a.k) ||
             ((a.kind == WALK_CHOSEN || a.kind == WALK_CHOSEN_THIN) && s - t > a.dot[t])) {
             t = (int)s;
-            cur = ls;
+            cur = rowcap ? (int64_t)(a.lptr[s + 1] - a.lptr[s]) : ls;
             targets++;
             top = 0;
             continue;
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
             }
             const int64_t c = valid ? (a.inj ? a.inj[r] : 2 * (int64_t)nd) : 0;
             const int64_t growth = valid ? (int64_t)nd + ne - (q1 - q0) : 0;
-            const int64_t pc = warp_incl_scan(c);
+            const int64_t pc = warp_incl_scan(rowcap ? (valid ? 1 : 0) : c);
             const int64_t pg = warp_incl_scan(growth);
             bool rules = true;
             if (valid && a.alpha > 0 && nd >= a.alpha) rules = false;
@@ -192,8 +197,8 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
             // a rule broken by an earlier lane stops the prefix there, like a cost overflow
             const unsigned badrule = __ballot_sync(0xffffffffu, !rules);
             const int first_bad = badrule ? __ffs(badrule) - 1 : 32;
-            const bool pass = (a.kind != WALK_NAIVE || (double)(cur + pc) <= a.avg) && (stored + pg <= a.limit) &&
-                              lane < first_bad;
+            const bool pass = (a.kind != WALK_NAIVE || (double)(cur + pc) <= a.avg) && (!rowcap || cur + pc <= a.k) &&
+                              (stored + pg <= a.limit) && lane < first_bad;
             const unsigned failmask = __ballot_sync(0xffffffffu, valid && !pass);
             const int first = failmask ? __ffs(failmask) - 1 : 32;
             const int nvalid = (int)(Bn - base < 32 ? Bn - base : 32);
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
                 int64_t rest = 0;
                 for (int64_t i2 = A + lane; i2 < Bn; i2 += 32) {
                     const int32_t r2 = a.lrows[i2];
-                    if (a.target[r2] == s) rest += a.row_cost[r2];
+                    if (a.target[r2] == s) rest += rowcap ? 1 : a.row_cost[r2];
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
@@ -483,8 +488,8 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
                            double avg, double cap, const int64_t* inj, int alpha, int64_t beta, int32_t* target,
                            PlanOut& po, cudaStream_t st) {
     const int64_t n = L->n, m = lv.m;
-    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || kind == WALK_CHOSEN_THIN || cap > 0 || inj ||
-                      alpha > 0 || beta > 0;
+    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || kind == WALK_CHOSEN_THIN || kind == WALK_ROWCAP ||
+                      cap > 0 || inj || alpha > 0 || beta > 0;
     if (!walk) {
         Scratch lt;
         SP_TRY(lt.alloc(std::max<int64_t>(1, m) * sizeof(int32_t), st));
@@ -761,9 +766,11 @@ extern "C" sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels
         dot_dev = dot.as<int32_t>();
     }
     int wk = kind == SPTRSV_STRATEGY_NAIVE ? WALK_NAIVE : kind == SPTRSV_STRATEGY_DEPTH_K ? WALK_DEPTH
-           : kind == SPTRSV_STRATEGY_CHOSEN ? WALK_CHOSEN : kind == SPTRSV_STRATEGY_MANUAL ? WALK_MANUAL : 0;
+           : kind == SPTRSV_STRATEGY_CHOSEN ? WALK_CHOSEN : kind == SPTRSV_STRATEGY_MANUAL ? WALK_MANUAL
+           : kind == SPTRSV_STRATEGY_ROWCAP ? WALK_ROWCAP : 0;
     if (!wk) { set_error("rewrite: unknown strategy %d", kind); return SPTRSV_ERR_INVALID; }
-    sptrsv_status rc = rewrite_system(L, lv, wk, sg->k, dot_dev, sg->avg_override, sg->nnz_growth_cap,
+    const int k = kind == SPTRSV_STRATEGY_ROWCAP && sg->k <= 0 ? ROWCAP_DEFAULT_ROWS : sg->k;
+    sptrsv_status rc = rewrite_system(L, lv, wk, k, dot_dev, sg->avg_override, sg->nnz_growth_cap,
                                       sg->growth_guard, sg->injected_cost_dev, sg->max_deps, sg->max_spread, out, st);
     if (rc == SPTRSV_OK) (*out)->strategy_used = kind;
     return rc;

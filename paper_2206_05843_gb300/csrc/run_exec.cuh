@@ -17,7 +17,7 @@
 // cycles, and a predicated-off one still takes its slot.  A fast block (every level within
 // 32 lanes of rows x right-hand sides x lanes per row, at most K_MAX FMAs per lane) runs exactly K
 // FMAs per lane and level, K fixed for the block: the staging pads each lane to K records
-// {coefficient, ring slot} with {0, zero slot}, and warp 0 runs a branch-free loop whose
+// (coefficient, ring slot) with (0, zero slot), and warp 0 runs a branch-free loop whose
 // per-level metadata is loaded one level ahead.
 #pragma once
 
@@ -84,6 +84,30 @@ struct RunGeom {
     int ring_rows, stage_rows, stage_entries;
 };
 
+// One staging buffer: 32 KB.  Two CTAs per SM (the persistent kernel's occupancy, which its
+// registers set) then leave about a third of the unified L1 / shared array to L1, which the
+// wide levels' per-lane vector loads use to merge the halves of each sector: larger buffers
+// (44 KB) shortened the thin-level block turnover but made wide levels slower (w2: 228 ->
+// 390 us) for the smaller L1.
+constexpr int64_t STAGE_BYTES = 32768;
+constexpr int STAGE_ENTRIES = 1536;
+
+// staging geometry for nrhs right-hand sides of vb-byte values: rows and coefficients of one
+// buffer, and an x ring of at least twice the staged rows
+inline RunGeom run_geometry(int nrhs, int vb) {
+    RunGeom g;
+    g.stage_entries = STAGE_ENTRIES;
+    g.stage_rows = (int)((STAGE_BYTES - (int64_t)g.stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
+    if (g.stage_rows < 16) {
+        g.stage_entries = 256;
+        g.stage_rows =
+            (int)std::max<int64_t>(16, (STAGE_BYTES - (int64_t)g.stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
+    }
+    g.ring_rows = 16;
+    while (g.ring_rows < 2 * g.stage_rows) g.ring_rows *= 2;
+    return g;
+}
+
 inline size_t run_stage_bytes(int vb, int nrhs, const RunGeom& g) {
     return (size_t)g.stage_rows * nrhs * vb + (size_t)g.stage_entries * (vb + 4) + (size_t)(3 * g.stage_rows + 2) * 4;
 }
@@ -99,24 +123,12 @@ inline size_t run_smem_bytes(int vb, int nrhs, const RunGeom& g) {
     return ((size_t)g.ring_rows * nrhs + RING_PAD) * vb + 2 * ((run_stage_bytes(vb, nrhs, g) + 15) / 16 * 16);
 }
 
-// one FMA step of one lane of a fast block: coefficient and ring slot of the dependency
-template <typename T>
-struct FastRec;
-template <>
-struct __align__(16) FastRec<double> {
-    double cv;
-    int32_t slot, pad;
-};
-template <>
-struct __align__(8) FastRec<float> {
-    float cv;
-    int32_t slot;
-};
-
-// records a staging buffer holds: they reuse the area of the compacted coefficients
-inline int fast_rec_capacity(int vb, const RunGeom& g) {
+// one FMA step of one lane of a fast block: the coefficient and the ring slot of its
+// dependency, kept as two arrays (T and 16-bit slot; a ring of at most 32,766 rows plus the zero
+// and dummy slots) in the area of the compacted coefficients
+__host__ __device__ inline int fast_rec_capacity(int vb, const RunGeom& g) {
     const int64_t bytes = (int64_t)g.stage_entries * (vb + 4) - 16;
-    return bytes > 0 ? (int)(bytes / (vb == 8 ? 16 : 8)) : 0;
+    return bytes > 0 ? (int)(bytes / (vb + 2)) : 0;
 }
 
 template <typename T>
@@ -125,7 +137,8 @@ struct RunSmem {
     T* bp;
     T* cval;
     int32_t* cslot;
-    FastRec<T>* rec;  // fast blocks: aliases cval / cslot
+    T* rcv;           // fast blocks: record coefficients (aliases cval / cslot)
+    uint16_t* rslot;  //   and record ring slots
     int32_t* cptr;
     int32_t* row;
     int32_t* lp;
@@ -144,7 +157,8 @@ struct RunSmem {
         bp = (T*)(base + ((size_t)g.ring_rows * nrhs + RING_PAD) * vb + buf * stage);
         cval = bp + (size_t)g.stage_rows * nrhs;
         cslot = (int32_t*)(cval + g.stage_entries);
-        rec = (FastRec<T>*)(((uintptr_t)cval + 15) & ~(uintptr_t)15);
+        rcv = (T*)(((uintptr_t)cval + 15) & ~(uintptr_t)15);
+        rslot = (uint16_t*)(rcv + fast_rec_capacity((int)vb, g));
         cptr = cslot + g.stage_entries;
         row = cptr + g.stage_rows + 1;
         lp = row + g.stage_rows;
@@ -217,7 +231,7 @@ __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0
         const int lb = sm.lp[lo], le = sm.lp[lo + 1];
         const int nlanes = (le - lb) * lpr;
         // records of level lo start at K * lpr * lb; step u of lane (g * lpr + e) at u * nlanes + lane
-        FastRec<T>* r = sm.rec + (size_t)K * lpr * lb + (size_t)(i - lb) * lpr;
+        const size_t r0 = (size_t)K * lpr * lb + (size_t)(i - lb) * lpr;  // this row's first record
         const int64_t p = P0 + i;
         const int q0 = v.cptr[p], q1 = v.cptr[p + 1];
         // a fast row has at most K * lpr entries: its loads go out QC at a time
@@ -239,9 +253,9 @@ __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0
                 const int32_t d = dd[u];
                 if (d >= ring_lo) {
                     if (j < steps) {
-                        FastRec<T>& e = r[(j / lpr) * nlanes + (j % lpr)];
-                        e.cv = cc[u];
-                        e.slot = d & mask;
+                        const size_t e = r0 + (size_t)(j / lpr) * nlanes + (j % lpr);
+                        sm.rcv[e] = cc[u];
+                        sm.rslot[e] = (uint16_t)(d & mask);
                     }
                     ++j;
                 } else {
@@ -250,9 +264,9 @@ __device__ void run_stage_b_fast(const SysView<T>& v, RunSmem<T>& sm, int64_t P0
             }
         }
         for (; j < steps; ++j) {
-            FastRec<T>& e = r[(j / lpr) * nlanes + (j % lpr)];
-            e.cv = T(0);
-            e.slot = sm.zero_slot;
+            const size_t e = r0 + (size_t)(j / lpr) * nlanes + (j % lpr);
+            sm.rcv[e] = T(0);
+            sm.rslot[e] = (uint16_t)sm.zero_slot;
         }
         sm.bp[(size_t)i * nrhs] = bp;
     }
@@ -369,8 +383,7 @@ struct FastOps {
 };
 
 struct FastLane {
-    int g, k, e, nrhs;  // row in the level, first right-hand side, coefficient lane
-    int lanes;          // lanes per row: LPR x (right-hand sides rounded up to a power of two) / RPL
+    int g, k, e, nrhs;  // row in the level, first right-hand side, coefficient lane, right-hand sides
 };
 
 // MR: several right-hand sides, RPL of them per lane (lane = (g * r2 / RPL + k / RPL) * LPR + e);
@@ -382,13 +395,12 @@ __device__ __forceinline__ void fast_load(const RunSmem<T>& sm, const FastLane& 
     const int rows = le - lb;
     const int nrec = rows * LPR;  // record lanes of the level (one per row and coefficient lane)
     const bool act = fl.g < rows && (!MR || fl.k < fl.nrhs);
-    const FastRec<T>* r = sm.rec + (size_t)K * LPR * lb + fl.g * LPR + fl.e;
+    const size_t r0 = (size_t)K * LPR * lb + fl.g * LPR + fl.e;
 #pragma unroll
     for (int u = 0; u < K; ++u) {
         if (act) {
-            const FastRec<T> e = r[u * nrec];
-            o.slot[u] = e.slot;
-            o.cv[u] = e.cv;
+            o.slot[u] = sm.rslot[r0 + u * nrec];
+            o.cv[u] = sm.rcv[r0 + u * nrec];
         } else {
             o.slot[u] = sm.zero_slot;
             o.cv[u] = T(0);
@@ -442,7 +454,6 @@ __device__ void run_compute_fast(RunSmem<T>& sm, int nrhs, int64_t P0, int l0, i
     fl.e = (int)threadIdx.x & (LPR - 1);
     fl.k = MR ? (((int)threadIdx.x / LPR) % kl) * RPL : 0;
     fl.g = (int)threadIdx.x / (LPR * kl);
-    fl.lanes = LPR * kl;
     auto lpb = [&](int li) { return li < nl ? sm.lp[li] : 0; };
     auto lpe = [&](int li) { return li < nl ? sm.lp[li + 1] : 0; };
     FastOps<T, K, RPL> oa, ob;
@@ -546,12 +557,39 @@ __device__ void run_write_out(const SysView<T>& v, const RunSmem<T>& sm, int64_t
 // compute -- write block i-1's x out of the ring and stage block i+1 into the other buffer.
 // Stage B of block i+1 reads from xp only x older than the ring window, which lies in
 // blocks <= i-1 (two blocks fit the ring), written out just before.
+// The stored arrays of a run of blocks are contiguous (positions [Pa, Pb), coefficients
+// [cptr[Pa], cptr[Pb])): one bulk L2 prefetch per array as the run starts, each capped, so that
+// staging reads L2 instead of DRAM.  Runs of one block skip it.
+constexpr int64_t RUN_PREFETCH_CAP = 24ll << 20;  // bytes per array
+
+template <typename T>
+__device__ void prefetch_run(const SysView<T>& v, int64_t Pa, int64_t Pb) {
+    auto cap = [](int64_t b) { return b < RUN_PREFETCH_CAP ? b : RUN_PREFETCH_CAP; };
+    const int64_t qa = v.cptr[Pa], qb = v.cptr[Pb];
+    l2_prefetch(v.perm + Pa, cap((Pb - Pa) * 4));
+    l2_prefetch(v.cptr + Pa, cap((Pb - Pa + 1) * 4));
+    l2_prefetch(v.ccol + qa, cap((qb - qa) * 4));
+    l2_prefetch(v.cval + qa, cap((qb - qa) * (int64_t)sizeof(T)));
+    if (v.bpre) {
+        l2_prefetch(v.bpre + Pa * v.nrhs, cap((Pb - Pa) * v.nrhs * (int64_t)sizeof(T)));
+    } else {
+        l2_prefetch(v.dinv + Pa, cap((Pb - Pa) * (int64_t)sizeof(T)));
+        if (v.eptr) {
+            const int64_t ea = v.eptr[Pa], eb = v.eptr[Pb];
+            l2_prefetch(v.eptr + Pa, cap((Pb - Pa + 1) * 4));
+            l2_prefetch(v.ecol + ea, cap((eb - ea) * 4));
+            l2_prefetch(v.eval + ea, cap((eb - ea) * (int64_t)sizeof(T)));
+        }
+    }
+}
+
 template <typename T, typename WaitFn>
 __device__ bool run_blocks(const SysView<T>& v, unsigned char* smem, RunGeom geo, const Lanes& ln, const int4* blocks,
                            int blk0, int blk1, WaitFn wait, unsigned long long* stamps) {
     if (blk0 >= blk1) return wait();
     const int64_t run_p0 = blocks[blk0].x;
     const int R = geo.ring_rows;
+    if (blk1 - blk0 > 1) prefetch_run(v, run_p0, (int64_t)blocks[blk1 - 1].y);
     {
         RunSmem<T> s0;
         s0.carve(smem, v.nrhs, geo, 0);

@@ -209,15 +209,9 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     if (sc.nrhs == nrhs && sc.lpr == lpr && sc.block == block && sc.run_width == s->run_width && sc.segs.p)
         return SPTRSV_OK;
     const int ngroups = block / lpr;
-    // shared memory: staging (~32 KB) + an x ring of at least twice the staged rows
-    int stage_entries = 1536;
-    int stage_rows = (int)((32768 - (int64_t)stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
-    if (stage_rows < 16) {
-        stage_entries = 256;
-        stage_rows = (int)std::max<int64_t>(16, (32768 - (int64_t)stage_entries * (vb + 4)) / ((int64_t)nrhs * vb + 12));
-    }
-    int ring_rows = 16;
-    while (ring_rows < 2 * stage_rows) ring_rows *= 2;
+    // shared memory: two staging buffers + an x ring of at least twice the staged rows
+    const RunGeom geo = run_geometry(nrhs, vb);
+    const int stage_entries = geo.stage_entries, stage_rows = geo.stage_rows, ring_rows = geo.ring_rows;
     int run_width = s->run_width > 0 ? s->run_width : (s->run_width < 0 ? 0 : ngroups);
     run_width = std::min(run_width, stage_rows);
     const int64_t m = s->m;

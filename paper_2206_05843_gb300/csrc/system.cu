@@ -94,11 +94,6 @@ __global__ void k_export_fill(int64_t n, const int32_t* pos, const int32_t* perm
     }
 }
 
-__global__ void k_copy_i64_to_i32(const int64_t* in, int32_t* out, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (int32_t)in[i];
-}
-
 }  // namespace
 
 sptrsv_status pack_system(sptrsv_system* s, const sptrsv_csr* L, const RewriteHeap* rwp, cudaStream_t st) {
@@ -225,6 +220,7 @@ sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info*
     if (!sc.segs.p) o->launches = 0;
     else if (sc.run_width == -2) o->launches = (int32_t)s->m;
     else o->launches = sc.h_segs.empty() ? 0 : 1 + sc.pre;
+    o->ctas = sc.segs.p ? sc.grid : 0;
     return SPTRSV_OK;
 }
 

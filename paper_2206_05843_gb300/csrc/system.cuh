@@ -8,6 +8,9 @@ namespace sp {
 // WIDE: one level over CTAs 0..w-1; RUN: staged blocks [y, z) on CTA 0
 enum SegType : int { SEG_WIDE = 0, SEG_RUN = 1 };
 
+// rows a ROWCAP target holds by default: the lanes of one warp, the fast executor's level width
+constexpr int ROWCAP_DEFAULT_ROWS = 32;
+
 // A segment of the persistent solve.  WIDE: one level split over CTAs 0..parts-1.
 // RUN: consecutive thin levels executed by CTA 0 alone, staged block by block.
 // int4 layout: {type, a, b, c}

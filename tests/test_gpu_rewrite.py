@@ -14,7 +14,7 @@ from tests.gpu_util import TOL_F32, TOL_F64, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-KIND = {B.NAIVE: O.NAIVE, B.DEPTH_K: O.DEPTH, B.CHOSEN: O.CHOSEN}
+KIND = {B.NAIVE: O.NAIVE, B.DEPTH_K: O.DEPTH, B.CHOSEN: O.CHOSEN, B.MANUAL: O.MANUAL, B.ROWCAP: O.ROWCAP}
 
 
 def run_both(m, kind, b=None, k=0, cap=0.0, depth_of_target=None, exact=True):
@@ -87,6 +87,23 @@ def test_chosen_depths_random():
     _, b = S.rhs_from_xtrue(m, 2, 3)
     run_both(m, B.CHOSEN, b, depth_of_target=dot)
     run_both(m, B.CHOSEN, b, depth_of_target=dot, cap=1.2)
+
+
+@pytest.mark.parametrize("k", [8, 32])
+@pytest.mark.parametrize("cap", [0.0, 1.5])
+def test_rowcap_plan_matches_oracle(k, cap):
+    """ROWCAP: plan, rewritten equations and solve identical to the oracle; every target
+    keeps at most k rows."""
+    m = S.gen_skewed(40000, 12, head=25000)
+    _, b = S.rhs_from_xtrue(m, 1, 4)
+    s, p = run_both(m, B.ROWCAP, b, k=k, cap=cap)
+    lev, _ = O.levels(m.rowptr, m.colidx)
+    moved = p.target != lev
+    assert moved.any()
+    assert np.bincount(p.target)[np.unique(p.target[moved])].max() <= k
+    mx = S.gen_mixture(30000, 10003)
+    _, b2 = S.rhs_from_xtrue(mx, 1, 5)
+    run_both(mx, B.ROWCAP, b2, k=k, cap=cap)
 
 
 def test_naive_skewed_small_and_mixture():
