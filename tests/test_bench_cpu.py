@@ -1,0 +1,43 @@
+"""Host-side arithmetic of bench.py on CPU: the dependent-FP64 chain floor and the algorithmic
+bytes of a solve, against hand counts on small systems."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+class FakeSystem:
+    """What chain_floor reads: the level count and the exported level / row pointer arrays."""
+
+    def __init__(self, level, cptr):
+        self.m = int(max(level) + 1) if len(level) else 0
+        self._ex = {"level": np.asarray(level, np.int32), "cptr": np.asarray(cptr, np.int64)}
+
+    def export(self):
+        return self._ex
+
+
+def test_chain_floor_counts_product_and_add_tree():
+    # level 0: two rows without dependencies (1 op); level 1: rows with 1 and 3 coefficients
+    # (longest 3 -> 1 + ceil(log2 3) = 3 ops); level 2: one row with 4 (1 + 2 = 3 ops)
+    level = [0, 0, 1, 1, 2]
+    cptr = [0, 0, 0, 1, 4, 8]
+    out = bench.chain_floor(FakeSystem(level, cptr), 1000.0)
+    assert out["levels"] == 3
+    assert out["dependent_fp64_ops"] == 1 + 3 + 3
+    assert abs(out["floor_us"] - 7 * bench.FP64_LATENCY_CYCLES / 1000.0) < 0.11
+
+
+def test_alg_bytes_plain_and_rewritten():
+    n, nnz_c = 10, 20
+    plain = {"nnz_c": nnz_c, "nnz_e": 0, "rows_moved": 0, "rewritten": 0}
+    # 4(n+1) + (4+v)(nnz_c + n) + 2 v n r
+    assert bench.alg_bytes(plain, n, 1) == 4 * 11 + 12 * 30 + 2 * 8 * 10
+    assert bench.alg_bytes(plain, n, 3, v=4) == 4 * 11 + 8 * 30 + 2 * 4 * 10 * 3
+    rw = {"nnz_c": nnz_c, "nnz_e": 7, "rows_moved": 4, "rewritten": 1}
+    # plus 4(n_rw + 1) + (4+v) nnz_e for the E rows
+    assert bench.alg_bytes(rw, n, 1) == bench.alg_bytes(plain, n, 1) + 4 * 5 + 12 * 7
