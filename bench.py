@@ -136,6 +136,19 @@ def make_workload(name):
 FP64_LATENCY_CYCLES = 64  # dependent float64 operation on GB300 (clock64 measurement)
 
 
+KERNEL_SOURCES = ["solve_kernel.cuh", "run_exec.cuh", "solve.cu", "internal.cuh", "system.cuh"]
+
+
+def kernel_sources_sha256() -> str:
+    """Fingerprint of the sources that define the solve kernel."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2206_05843_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def chain_floor(sysm, sm_mhz: float) -> dict:
     """Dependency-chain floor of a level-set solve: every level needs, after its last
     dependency is known, one product and a tree of ceil(log2 k) adds over the k coefficients
@@ -416,11 +429,17 @@ def run_ours(args):
     by_pl = alg_bytes(info_pl, m.n, nrhs)
     gbs_rw = by_rw / (us_rw * 1e-6) / 1e9
     gbs_pl = by_pl / (us_plain * 1e-6) / 1e9
-    traffic = None
+    # DRAM traffic of the timed launch from an ncu capture, valid only for the kernel sources it
+    # was captured with (their sha256 is stored beside the figures)
+    traffic, traffic_note = None, None
     tfile = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
     if os.path.exists(tfile):
         try:
-            traffic = json.load(open(tfile)).get(used)
+            tj = json.load(open(tfile))
+            if tj.get("kernel_sources_sha256") == kernel_sources_sha256():
+                traffic = tj.get(used)
+            else:
+                traffic_note = "stale: the solve kernel changed after the ncu capture"
         except (OSError, ValueError):
             traffic = None
     sm_mhz = float(clk.get("sm_mhz") or 0) if isinstance(clk, dict) else 0.0
@@ -474,7 +493,7 @@ def run_ours(args):
             "parallelism": "replicas" if world > 1 else "1 GPU",
         },
         "roofline": {"bound": "hbm", "achieved": round(gbs_rw, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(gbs_rw / peak, 5), "traffic": traffic,
+                     "frac": round(gbs_rw / peak, 5), "traffic": traffic, "traffic_note": traffic_note,
                      "peak_source": f"{peak_src} copy bandwidth", "kernel": "k_solve<double>",
                      "alg_bytes_per_launch": by_rw},
         "critical_path": crit,

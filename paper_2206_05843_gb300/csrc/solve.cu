@@ -262,11 +262,17 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
             l = l1;
         } else {
             int64_t w = lp[l + 1] - lp[l];
-            int64_t per = std::max<int64_t>((w + gmax - 1) / gmax, ngroups);
+            // lanes per row of this level: with one lane per row, a moderately wide level of
+            // longer rows takes two, halving each row's dependent float64 chain; very wide levels
+            // keep one (they are bound by float64 issue, where the extra add costs)
+            int wl = lpr;
+            if (nrhs == 1 && lpr == 1 && w <= 65536 && (int64_t)hcptr[lp[l + 1]] - hcptr[lp[l]] >= 4 * w) wl = 2;
+            const int64_t ng = block / wl;
+            int64_t per = std::max<int64_t>((w + gmax - 1) / gmax, ng);
             int64_t parts = (w + per - 1) / per;
             if (per >= INT32_MAX) { set_error("level too wide"); return SPTRSV_ERR_UNSUPPORTED; }
             max_parts = std::max(max_parts, parts);
-            sc.h_segs.push_back(make_int4(SEG_WIDE, (int)l, (int)per, (int)parts));
+            sc.h_segs.push_back(make_int4(SEG_WIDE | (wl == lpr ? 0 : wl << SEG_LPR_SHIFT), (int)l, (int)per, (int)parts));
             ++l;
         }
     }

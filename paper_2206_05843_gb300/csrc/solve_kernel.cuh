@@ -23,7 +23,7 @@ template <typename T>
 __device__ bool wait_segment(const SolveArgs<T>& a, int s) {
     if (s < 0) return true;
     int4 sg = a.segs[s];
-    int parts = sg.x == SEG_WIDE ? sg.w : 1;
+    int parts = (sg.x & SEG_TYPE_MASK) == SEG_WIDE ? sg.w : 1;
     bool failed = false;
     for (int t = threadIdx.x; t < parts && !failed; t += blockDim.x) {
         const int* f = a.flags + t;
@@ -313,16 +313,20 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
 
     for (int s = 0; s < a.nseg; ++s) {
         const int4 sg = a.segs[s];
-        if (sg.x == SEG_WIDE) {
+        if ((sg.x & SEG_TYPE_MASK) == SEG_WIDE) {
             if (me >= sg.w) continue;
             const int l = sg.y;
             const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
             const int64_t my0 = p0 + (int64_t)me * sg.z;
             const int64_t my1 = min(p1, my0 + (int64_t)sg.z);
-            if (nrhs == 1 && a.lpr == 1) {
+            const int wl = (sg.x >> SEG_LPR_SHIFT) > 0 ? (sg.x >> SEG_LPR_SHIFT) : a.lpr;
+            if (nrhs == 1 && wl == 1) {
                 if (!wide_rows_1rhs(a, my0, my1, s)) return;
-            } else {
+            } else if (wl == a.lpr) {
                 if (!wide_rows_general(a, ln, ngroups, grp, my0, my1, s)) return;
+            } else {
+                const Lanes lw = make_lanes(wl, nrhs);
+                if (!wide_rows_general(a, lw, (int)blockDim.x / wl, (int)threadIdx.x / wl, my0, my1, s)) return;
             }
             publish(a, s);
             if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());

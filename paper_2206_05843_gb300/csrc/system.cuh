@@ -5,8 +5,10 @@
 
 namespace sp {
 
-// WIDE: one level over CTAs 0..w-1; RUN: staged blocks [y, z) on CTA 0
+// WIDE: one level over CTAs 0..w-1; RUN: staged blocks [y, z) on CTA 0.  The type is in the low
+// byte of a segment's x; a WIDE segment keeps its lanes per row above it (0: the schedule's)
 enum SegType : int { SEG_WIDE = 0, SEG_RUN = 1 };
+constexpr int SEG_TYPE_MASK = 0xff, SEG_LPR_SHIFT = 8;
 
 // rows a ROWCAP target holds by default: the lanes of one warp, the fast executor's level width
 constexpr int ROWCAP_DEFAULT_ROWS = 32;
