@@ -131,7 +131,8 @@ enum {
 
 typedef struct {
     int32_t kind;                  /* SPTRSV_STRATEGY_* */
-    int32_t k;                     /* DEPTH_K / MANUAL: levels merged into each target */
+    int32_t k;                     /* DEPTH_K / MANUAL: levels merged into each target; ROWCAP: rows a target may
+                                      hold (<= 0: 32) */
     double nnz_growth_cap;         /* > 0: nnz(L') + nnz(E) <= cap * nnz(L); <= 0: no cap */
     double avg_override;           /* > 0: use this avgLevelCost instead of the computed one */
     double growth_guard;           /* > 0: fail with SPTRSV_ERR_NUMERIC if a rewritten coefficient exceeds it in magnitude */
