@@ -238,6 +238,20 @@ sptrsv_status sptrsv_solve_noalloc(const sptrsv_system* s, const void* b_dev, vo
  * solve (SPTRSV_OK or SPTRSV_ERR_TIMEOUT), then clears it. */
 sptrsv_status sptrsv_solve_status(const sptrsv_system* s, sptrsv_stream_t stream);
 
+/* Test hook (the paper has no counterpart): the host block cutter of the single-CTA executor, on
+ * host arrays, no device work.  level_ptr_host[m+1] and cptr_host[n+1] (n = level_ptr_host[m]) are
+ * the level pointer and the coefficient row pointer of a system in stored (level) order; nrhs,
+ * lanes_per_row and value_bytes (4 or 8) select the staging geometry, written to geometry_out[4] =
+ * {stage rows, stage entries, ring rows, fast-block records} when not NULL.  Blocks go to
+ * blocks_host[4 * capacity] as {first position, end position, first level, levels | flags} with
+ * flags 1 << 30 (narrow), 1 << 29 (fast) and K (FMA steps per lane) in bits 26..28; *count_out
+ * receives the number of blocks.  SPTRSV_ERR_INVALID when capacity is too small (count set),
+ * SPTRSV_ERR_UNSUPPORTED when a row has more coefficients than a staging buffer holds. */
+sptrsv_status sptrsv_debug_run_blocks(const int32_t* level_ptr_host, int64_t m, const int32_t* cptr_host,
+                                      int32_t nrhs, int32_t lanes_per_row, int32_t value_bytes,
+                                      int32_t* blocks_host, int64_t capacity, int64_t* count_out,
+                                      int32_t* geometry_out);
+
 /* Test hook for the bounded waits: the CTA that finishes schedule segment `segment`
  * does not publish it, so every wait on it runs out after timeout_ns.  segment < 0
  * disables the hook; timeout_ns <= 0 restores the default (2 s). */

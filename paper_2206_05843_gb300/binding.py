@@ -33,7 +33,7 @@ EXPORTED = [
     "sptrsv_batch_info_get", "sptrsv_batch_destroy", "sptrsv_picker_create", "sptrsv_picker_destroy",
     "sptrsv_picker_get_params", "sptrsv_picker_set_params", "sptrsv_picker_set_norm", "sptrsv_picker_save",
     "sptrsv_picker_load", "sptrsv_picker_features", "sptrsv_picker_infer", "sptrsv_picker_grad",
-    "sptrsv_picker_train_step",
+    "sptrsv_picker_train_step", "sptrsv_debug_run_blocks",
 ]
 
 
@@ -104,6 +104,7 @@ def load():
             "sptrsv_solve_status": [vp, vp],
             "sptrsv_solve_noalloc": [vp, vp, vp, i32, i64, vp],
             "sptrsv_debug_set_wait": [vp, i64, i64],
+            "sptrsv_debug_run_blocks": [vp, i64, vp, i32, i32, i32, vp, i64, vp, vp],
             "sptrsv_system_tune": [vp, i32, i32, i32],
             "sptrsv_system_autotune": [vp, i32, vp, vp],
             "sptrsv_upper_to_lower": [vp, vp, vp, vp, vp],
@@ -497,3 +498,24 @@ def features(matrix: Matrix, levels: Levels, depths=DEFAULT_DEPTHS):
     check(load().sptrsv_picker_features(C.byref(matrix.csr), levels.h, d.ctypes.data_as(C.c_void_p), d.size,
                                         _ptr(out), _stream()))
     return out[:levels.m * d.size]
+
+
+def run_blocks(level_ptr, cptr, nrhs=1, lanes_per_row=1, value_bytes=8):
+    """The host block cutter of the single-CTA executor (test hook): returns (blocks int32[k, 4],
+    geometry {stage_rows, stage_entries, ring_rows, fast_records})."""
+    lp = np.ascontiguousarray(level_ptr, dtype=np.int32)
+    cp = np.ascontiguousarray(cptr, dtype=np.int32)
+    geo = np.zeros(4, np.int32)
+    cnt = C.c_int64(0)
+    cap = max(16, lp.size)
+    while True:
+        out = np.zeros((cap, 4), np.int32)
+        rc = load().sptrsv_debug_run_blocks(lp.ctypes.data, lp.size - 1, cp.ctypes.data, nrhs, lanes_per_row,
+                                            value_bytes, out.ctypes.data, cap, C.byref(cnt), geo.ctypes.data)
+        if rc == ERR_INVALID and cnt.value > cap:
+            cap = cnt.value
+            continue
+        check(rc)
+        break
+    g = dict(zip(("stage_rows", "stage_entries", "ring_rows", "fast_records"), (int(v) for v in geo)))
+    return out[:cnt.value].copy(), g

@@ -456,3 +456,42 @@ sptrsv_status time_solve_us(sptrsv_system* s, int reps, double* us, cudaStream_t
     return sptrsv_solve_status(s, st);
 }
 }  // namespace sp
+
+// Test hook: the host block cutter on caller arrays (no device work).
+extern "C" sptrsv_status sptrsv_debug_run_blocks(const int32_t* level_ptr_host, int64_t m, const int32_t* cptr_host,
+                                                 int32_t nrhs, int32_t lanes_per_row, int32_t value_bytes,
+                                                 int32_t* blocks_host, int64_t capacity, int64_t* count_out,
+                                                 int32_t* geometry_out) {
+    using namespace sp;
+    if (!level_ptr_host || !cptr_host || !count_out || m < 0 || nrhs < 1 || lanes_per_row < 1 ||
+        (value_bytes != 4 && value_bytes != 8)) {
+        set_error("debug_run_blocks: invalid argument");
+        return SPTRSV_ERR_INVALID;
+    }
+    const RunGeom g = run_geometry(nrhs, value_bytes);
+    const int recs = fast_rec_capacity(value_bytes, g);
+    if (geometry_out) {
+        geometry_out[0] = g.stage_rows;
+        geometry_out[1] = g.stage_entries;
+        geometry_out[2] = g.ring_rows;
+        geometry_out[3] = recs;
+    }
+    std::vector<int4> out;
+    if (m > 0 && build_run_blocks(level_ptr_host, cptr_host, 0, m, g.stage_rows, g.stage_entries, lanes_per_row, nrhs,
+                                  recs, out) != 0) {
+        set_error("debug_run_blocks: a row has more coefficients than the staging area");
+        return SPTRSV_ERR_UNSUPPORTED;
+    }
+    *count_out = (int64_t)out.size();
+    if ((int64_t)out.size() > capacity || (!blocks_host && !out.empty())) {
+        set_error("debug_run_blocks: %zu blocks, capacity %lld", out.size(), (long long)capacity);
+        return SPTRSV_ERR_INVALID;
+    }
+    for (size_t i = 0; i < out.size(); ++i) {
+        blocks_host[4 * i] = out[i].x;
+        blocks_host[4 * i + 1] = out[i].y;
+        blocks_host[4 * i + 2] = out[i].z;
+        blocks_host[4 * i + 3] = out[i].w;
+    }
+    return SPTRSV_OK;
+}
