@@ -100,12 +100,13 @@ def test_plain_solve_schedule_variants(run_width, lpr):
     solve_and_compare(m, b, TOL_F64, tune=dict(run_width=run_width, lanes_per_row=lpr))
 
 
-@pytest.mark.parametrize("nrhs", [2, 5, 16, 32])
+@pytest.mark.parametrize("nrhs", [2, 5, 16, 17, 29, 32])
 @pytest.mark.parametrize("lpr", [1, 2])
 @pytest.mark.parametrize("f32", [False, True])
 def test_fast_thin_levels_several_rhs(nrhs, lpr, f32):
     """Thin levels with several right-hand sides in the fast executor (one lane per row,
-    right-hand side and coefficient lane), plain and rewritten, against the oracle; the
+    right-hand side and coefficient lane; two right-hand sides per lane above 16, the last
+    lane of an odd count holding one), plain and rewritten, against the oracle; the
     dependencies older than the ring window are folded for every right-hand side."""
     m = S.gen_skewed(30000, 8, head=12000)
     if f32:
