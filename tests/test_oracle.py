@@ -228,9 +228,30 @@ def test_rewrite_is_elimination_E_times_L(seed, kind, k):
     """Every rewritten row is a combination of original rows: A = F L, where the columns
     the rewrite removed become (numerically) zero."""
     m = small_random_lower(60, 0.08, seed)
-    L = m.to_dense()
     lev, mm = O.levels(m.rowptr, m.colidx)
-    p = O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k)
+    check_elimination(m, lev, mm, O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k), seed)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("kind", ["manual", "chosen", "chosen_thin", "rowcap", "rowcap_cap"])
+def test_rewrite_is_elimination_for_every_planner(seed, kind):
+    """The same identities for the other planners: MANUAL, per-target depths (all levels or
+    thin levels only) and ROWCAP, with and without the nnz cap."""
+    m = small_random_lower(80, 0.06, seed + 100)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    dot = np.random.default_rng(seed).integers(0, 6, mm).astype(np.int32)
+    p = {"manual": lambda: O.plan(m.rowptr, m.colidx, lev, mm, O.MANUAL, k=3),
+         "chosen": lambda: O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN, depth_of_target=dot),
+         "chosen_thin": lambda: O.plan(m.rowptr, m.colidx, lev, mm, O.CHOSEN_THIN, depth_of_target=dot),
+         "rowcap": lambda: O.plan(m.rowptr, m.colidx, lev, mm, O.ROWCAP, k=6),
+         "rowcap_cap": lambda: O.plan(m.rowptr, m.colidx, lev, mm, O.ROWCAP, k=6, cap=1.2)}[kind]()
+    check_elimination(m, lev, mm, p, seed)
+    if kind == "rowcap_cap":
+        assert p.stored_nnz <= 1.2 * p.nnz_l
+
+
+def check_elimination(m, lev, mm, p, seed):
+    L = m.to_dense()
     sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, p.target)
     A, F = dense_system(sy, m.n)
     assert np.allclose(F @ L, A, rtol=0, atol=1e-13)
