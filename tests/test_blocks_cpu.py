@@ -84,3 +84,25 @@ def test_block_cutter_splits_a_level_too_large_for_the_stage():
     blocks, g = check_blocks(lp, cptr, 1, 1, 8)
     assert len(blocks) >= 2 and not (blocks[1:, 3] & FAST).any()
     assert (blocks[:, 1] - blocks[:, 0]).max() <= g["stage_rows"]
+
+
+def test_block_cutter_random_structures():
+    """Random level widths (1..70 rows) and row lengths (0..20 coefficients): the invariants hold
+    for every lanes / right-hand-side choice the executor supports."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(widths=st.lists(st.integers(1, 70), min_size=1, max_size=120),
+               seed=st.integers(0, 2**31 - 1),
+               cfg=st.sampled_from([(1, 1, 8), (1, 2, 8), (1, 4, 8), (2, 1, 8), (20, 2, 8), (1, 1, 4), (7, 2, 4)]))
+    def run(widths, seed, cfg):
+        rng = np.random.default_rng(seed)
+        n = int(sum(widths))
+        lp = np.concatenate([[0], np.cumsum(widths)]).astype(np.int32)
+        length = rng.integers(0, 21, n)
+        length[: widths[0]] = 0  # the first level has no dependencies
+        cptr = np.concatenate([[0], np.cumsum(length)]).astype(np.int32)
+        check_blocks(lp, cptr, *cfg)
+
+    run()
