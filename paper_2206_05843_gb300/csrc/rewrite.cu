@@ -297,7 +297,7 @@ struct FillArgs {
     int32_t* e_cnt;
     int32_t* hcol;
     double* hval;
-    int64_t* ub;  // per row: upper bound of C + E entries this round (0 for other rows)
+    int64_t* ub;  // per row: upper bound of C + E entries in this depth round (0 for other rows)
     int64_t* ubc;
     int32_t* tcol;  // per-round temporary of the merge sort (same offsets as the round's rows)
     double* tval;
