@@ -209,8 +209,6 @@ def run_reference(args):
     if rank != 0:
         return 0
     m, b, _ = make_workload(args.workload)
-    for _ in range(max(0, args.warmup)):
-        pass
     # each step one whole oracle solve of the workload
     import oracle as O
     O.build()
