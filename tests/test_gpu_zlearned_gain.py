@@ -1,0 +1,60 @@
+"""The learned gain of the committed trained picker on held-out mixtures (timed on the GPU;
+after the parity files, so that a slow or noisy box cannot hide them)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2206_05843_gb300 import binding as B
+from paper_2206_05843_gb300 import synth as S
+from tests.gpu_util import TOL_F64, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _median_solve_us(sysm, bt, reps=9):
+    torch = torch_cuda()
+    x = torch.empty_like(bt)
+    for _ in range(2):
+        sysm.solve(bt, x)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sysm.solve(bt, x)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3)
+    sysm.status()
+    return float(np.median(ts)), x
+
+
+def test_trained_picker_gain_on_held_out_mixtures():
+    """The learned gain with the committed trained picker, on the first three held-out mixtures
+    (seeds 20,000+, sizes drawn as in the evaluation): the learned strategy is at least as fast as
+    the paper's naive strategy (10% timing tolerance), clearly faster than the plain solve on each
+    matrix and by 1.3x in geometric mean, and exact to 1e-10."""
+    torch = torch_cuda()
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2206_05843_gb300",
+                        "picker_trained.bin")
+    pk = B.Picker.load(path)
+    erng = S.rng_for(54321)
+    gains = []
+    for i in range(3):
+        n = int(round(np.exp(erng.uniform(np.log(100_000), np.log(1_000_000)))))
+        m = S.gen_mixture(n, 20_000 + i)
+        xt, b = S.rhs_from_xtrue(m, 1, 7)
+        M = B.Matrix.from_host(m)
+        lv = B.Levels(M)
+        bt = torch.from_numpy(b[0]).cuda()
+        t_plain, _ = _median_solve_us(B.System(M, lv), bt)
+        t_naive, _ = _median_solve_us(B.System(M, lv, B.NAIVE, cap=1.5), bt)
+        learned = B.System(M, lv, B.LEARNED, cap=1.5, picker=pk)
+        t_learned, x = _median_solve_us(learned, bt)
+        assert rel_l2(x.cpu().numpy(), xt[0]) < TOL_F64
+        assert t_learned <= 1.10 * t_naive, (i, t_learned, t_naive, learned.info["strategy_used"])
+        assert t_plain / t_learned >= 1.15, (i, t_plain, t_learned)
+        gains.append(t_plain / t_learned)
+    assert float(np.exp(np.mean(np.log(gains)))) >= 1.3, gains
