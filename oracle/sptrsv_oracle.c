@@ -18,16 +18,22 @@
  *   orc_level_stats       row cost 2*nnz-1 and level cost 2*sum(nnz)-n (Section III).
  *   orc_plan              the rewrite planner of Section III: the naive avgLevelCost
  *                         strategy, the fixed-distance ("every k levels into the next
- *                         target") strategy, and per-target depths chosen by a caller.
+ *                         target") strategy, the manual strategy (fixed distance over thin
+ *                         levels), per-target depths chosen by a caller (over all levels or
+ *                         thin levels only), the row-capped walk (a row count in place of
+ *                         avgLevelCost), the nnz cap and the per-row rules of Section III.A.
+ *                         Pinned by the Section III costMap example and structural
+ *                         identities; on general inputs beyond those its choices are parity
+ *                         unpinned against the paper (Table I needs datasets that are missing).
  *   orc_rewrite           equation rewriting with rearrangement (Section II.B, Fig. 2):
  *                         substitute every dependency that sits on the target level or
  *                         below it by its own equation, then group the coefficients of
  *                         each unknown and of each b entry.
  *   orc_solve_rewritten   forward substitution of the rewritten equations.
  *
- * Readings where the paper is silent or garbled are the ones recorded in the design
- * notes: 0-based levels, rewritten-row cost 2*|deps|, greedy prefix stop rule, fixed
- * average, fat levels break a run, structural (not numerical) fill.
+ * Readings where the paper is silent or garbled: 0-based levels, rewritten-row cost
+ * 2*|deps|, greedy prefix stop rule, fixed average, fat levels break a run, structural (not
+ * numerical) fill, the nnz cap and the per-row rules checked in planning order.
  */
 #include <math.h>
 #include <stdint.h>
