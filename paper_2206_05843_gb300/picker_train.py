@@ -9,8 +9,9 @@ g+1 levels (under the nnz cap) and solved with stamps.  For a target level t the
 and the sample's input is the 12-feature vector of candidate (t, g) computed on the
 original matrix.  Training runs the library's own MLP forward, backward and Adam kernels.
 
-Evaluation (held-out matrices): solve time of the learned strategy against the paper's
-naive strategy and against no rewrite, with the residual of each.
+Evaluation (held-out matrices): solve time of the learned strategy (and of the model's plan
+alone) against the paper's naive strategy, the row-capped plan and no rewrite, with the
+residual of each.
 
 Usage: python -m paper_2206_05843_gb300.picker_train --train 600 --heldout 200 --out picker.bin
 """
@@ -153,6 +154,7 @@ def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
         ref = xt[0]
         res = {"n": m.n, "levels": lv.m}
         for name, kw in (("none", {}), ("naive", dict(kind=B.NAIVE, cap=cap)),
+                         ("rowcap", dict(kind=B.ROWCAP, k=32, cap=cap)),
                          ("learned", dict(kind=B.LEARNED, cap=cap, picker=pk)),
                          ("learned_model_only", dict(kind=B.LEARNED, cap=cap, picker=pk, model_only=True))):
             s = B.System(M, lv, **kw)
@@ -165,14 +167,16 @@ def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
     def gmean(key):
         return float(np.exp(np.mean([np.log(r["none"]["us"] / r[key]["us"]) for r in rows])))
     summary = {"matrices": len(rows),
-               "geomean_speedup_vs_none": {"naive": gmean("naive"), "learned": gmean("learned"),
+               "geomean_speedup_vs_none": {"naive": gmean("naive"), "rowcap": gmean("rowcap"),
+                                           "learned": gmean("learned"),
                                            "learned_model_only": gmean("learned_model_only")},
                "geomean_speedup_learned_vs_naive": float(np.exp(np.mean(
                    [np.log(r["naive"]["us"] / r["learned"]["us"]) for r in rows]))),
                "geomean_speedup_model_only_vs_naive": float(np.exp(np.mean(
                    [np.log(r["naive"]["us"] / r["learned_model_only"]["us"]) for r in rows]))),
                "model_plan_kept": int(sum(r["learned"]["strategy_used"] == B.CHOSEN for r in rows)),
-               "max_rel_err": max(max(r[k]["rel_err"] for k in ("none", "naive", "learned", "learned_model_only"))
+               "max_rel_err": max(max(r[k]["rel_err"] for k in ("none", "naive", "rowcap", "learned",
+                                                                "learned_model_only"))
                                   for r in rows)}
     return rows, summary
 
