@@ -58,3 +58,22 @@ def test_trained_picker_gain_on_held_out_mixtures():
         assert t_plain / t_learned >= 1.15, (i, t_plain, t_learned)
         gains.append(t_plain / t_learned)
     assert float(np.exp(np.mean(np.log(gains)))) >= 1.3, gains
+
+
+def test_bench_configuration_full_size_matches_oracle():
+    """The configuration bench.py times, at full size: the skewed n = 1,000,000 matrix, the
+    learned strategy with the trained picker under the 1.5 nnz cap, the autotuned schedule;
+    the solution against the oracle's forward substitution of the original system."""
+    import oracle as O
+    torch = torch_cuda()
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2206_05843_gb300",
+                        "picker_trained.bin")
+    m, b, xt = S.gen_config("c1")
+    M = B.Matrix.from_host(m)
+    lv = B.Levels(M)
+    s = B.System(M, lv, B.LEARNED, cap=1.5, picker=B.Picker.load(path))
+    s.autotune(1)
+    assert s.info["stored_nnz"] <= 1.5 * s.info["nnz_l"]
+    x = s.solve(torch.from_numpy(b).cuda(), check_status=True).cpu().numpy()
+    assert rel_l2(x, O.forward_subst(m.rowptr, m.colidx, m.vals, b)) < TOL_F64
+    assert rel_l2(x, xt) < 1e-12
