@@ -118,7 +118,7 @@ def test_naive_skewed_small_and_mixture():
 def test_naive_config1_full_size():
     m, b, _ = S.gen_config("c1")
     s, p = run_both(m, B.NAIVE, b, cap=1.5)
-    assert s.m == p.levels_after or s.m <= p.levels_after
+    assert s.m == p.levels_after  # re-levelling keeps exactly the planned non-empty levels
 
 
 @pytest.mark.parametrize("k", [1, 2, 4])
@@ -149,6 +149,20 @@ def test_costmap_example_on_gpu():
                     injected_cost=torch.from_numpy(inj.astype(np.int64)).cuda())
     ex = sysm.export()
     assert ex["target"].tolist() == [g["expected_target"][str(i)] for i in range(n)]
+
+
+@pytest.mark.parametrize("name", ["equality", "over", "zero"])
+def test_naive_rewritten_row_cost_hand_derived_on_gpu(name):
+    """The GPU planner's own cost of a rewritten row (2 |D'|, no injected cost, computed average)
+    reproduces the hand-derived plans of tests/naive_cost_cases.py."""
+    from tests.naive_cost_cases import CASES, csr_arrays, expected_target
+    case = CASES[name]
+    n, counts, cols = csr_arrays(case)
+    m = S.gen_from_deps(n, np.array(counts), np.array(cols, dtype=np.int64), S.rng_for(3))
+    _, b = S.rhs_from_xtrue(m, 1, 5)
+    s, p = run_both(m, B.NAIVE, b)
+    assert s.export()["target"].tolist() == expected_target(case)
+    assert s.info["avg_cost"] == pytest.approx(case["avg"], abs=1e-9)
 
 
 def test_growth_guard_trips_on_far_rewrite_of_small_pivots():

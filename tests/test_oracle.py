@@ -506,3 +506,33 @@ def test_planner_per_row_rules(alpha, beta):
         loose = O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k, alpha=10**6, beta=10**9)
         assert np.array_equal(free.target, loose.target)
         assert p.moved <= free.moved or kind == O.NAIVE
+
+
+# ---------------------------------------------------------------------------------
+# the cost of a rewritten row (Section III row cost, Section IV: division folded in)
+# ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["equality", "over", "zero"])
+def test_planner_naive_rewritten_row_cost_hand_derived(name):
+    """NAIVE plans worked out by hand (tests/naive_cost_cases.py) with no injected cost and no
+    avg override: the planner's own cost of a rewritten row, 2 |D'|, decides them.  Charging
+    2 |D'| + 1 changes the plan of EQUALITY and ZERO, 2 |D'| - 1 that of OVER."""
+    from tests.naive_cost_cases import CASES, csr_arrays, expected_row_cost, expected_target
+    case = CASES[name]
+    n, counts, cols = csr_arrays(case)
+    m = S.gen_from_deps(n, np.array(counts), np.array(cols, dtype=np.int64), S.rng_for(3))
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    st = O.level_stats(m.rowptr, lev, mm)
+    assert [int(c) for c in st["cost"]] == case["level_cost"]
+    p = O.plan(m.rowptr, m.colidx, lev, mm, O.NAIVE)
+    assert p.avg == pytest.approx(case["avg"], abs=1e-9)
+    assert p.target.tolist() == expected_target(case)
+    assert p.row_cost.tolist() == expected_row_cost(case)
+    assert p.levels_after == case["levels_after"]
+    for lvl, cost in case["target_level_cost"].items():
+        assert int(p.row_cost[p.target == lvl].sum()) == cost
+    # the dependency counts the costs were derived from are those of the rewritten equations
+    sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, p.target)
+    for r, d in case["deps_after"].items():
+        assert int(sy.cptr[r + 1] - sy.cptr[r]) == d
+        assert p.row_cost[r] == 2 * d
