@@ -12,6 +12,15 @@ timed region and their times are reported separately.  The working set (about 12
 close to the L2 size, so L2 is flushed (a 512 MB write) before every timed solve, outside
 the event pair that times the solve.
 
+Beside the headline the same line carries, under "workloads" (and as scalars in "config"),
+the other configurations, each autotuned and timed the same way (mean of the steps, L2
+flushed before each): the wide-level matrices w1 (2048 x 2048 grid in red-black order, 1 and
+16 right-hand sides) and w2 (8 layers x 524,288 rows, 8 dependencies), where the HBM
+roofline fraction is the figure of merit; the natural-order 2048 x 2048 grid c2 with 1 and
+16 right-hand sides, plain (k0) and rewritten at depths 1, 2 and 4; and the 256-matrix batch
+c3 as one graph replay per step.  With the trained picker, "learned_vs_alternatives" holds the
+network's own plan and the naive plan on c1, timed like the headline.
+
 --impl reference times the CPU oracle (serial float64 forward substitution) instead.
 """
 from __future__ import annotations
@@ -46,6 +55,8 @@ def parse():
     ap.add_argument("--strategy", default="auto", choices=["auto", "naive", "learned", "depth1", "depth2", "depth4"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extra", default="w1,w1r16,w2,c2,c3",
+                    help="workloads measured beside the headline (comma list of w1, w1r16, w2, c2, c3; 'none')")
     return ap.parse_args()
 
 
@@ -330,6 +341,140 @@ def level_handoffs(torch, sysm, bt, xt) -> dict:
     return out
 
 
+def timed_us(torch, fn, steps, warmup, flush, stream):
+    """Mean and median device time (us) of `steps` calls of fn, L2 flushed before each, CUDA
+    events on the launching stream around the call only."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return statistics.mean(ms) * 1e3, statistics.median(ms) * 1e3
+
+
+def rel_residual(m, x, b) -> float:
+    """max over right-hand sides of ||L x - b|| / ||b|| in float64 (a sparse product, plain numpy)."""
+    rp = m.rowptr.astype(np.int64)
+    rowid = np.repeat(np.arange(m.n), np.diff(rp))
+    vals = m.vals.astype(np.float64)
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    b = np.atleast_2d(np.asarray(b, dtype=np.float64))
+    out = 0.0
+    for k in range(b.shape[0]):
+        r = np.bincount(rowid, weights=vals * x[k][m.colidx], minlength=m.n) - b[k]
+        out = max(out, float(np.linalg.norm(r) / max(np.linalg.norm(b[k]), 1e-300)))
+    return out
+
+
+def measure_single(torch, B, m, b, xt, kw, steps, warmup, flush, stream, peak):
+    """One system of one workload: autotuned for its right-hand sides, mean solve time with L2
+    flushed, algorithmic bytes, GB/s and the fraction of the HBM peak, error against x_true
+    (or the relative residual when b is not built from a known x)."""
+    M = B.Matrix.from_host(m)
+    lv = B.Levels(M)
+    s = B.System(M, lv, **kw)
+    nrhs = b.shape[0]
+    s.autotune(nrhs)
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    x = torch.empty_like(bt)
+    s.solve(bt, x, check_status=True)
+    xx = x.cpu().numpy()
+    us, med = timed_us(torch, lambda: s.solve(bt, x), steps, warmup, flush, stream)
+    s.status()
+    info = s.refresh()
+    by = alg_bytes(info, m.n, nrhs, 8 if m.vals.dtype == np.float64 else 4)
+    gbs = by / (us * 1e-6) / 1e9
+    out = {"us": round(us, 2), "median_us": round(med, 2), "levels": int(info["m"]), "alg_bytes": by,
+           "gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4), "launches": int(info["launches"])}
+    if xt is not None:
+        out["rel_err_vs_x_true"] = float(np.linalg.norm(xx - xt) / np.linalg.norm(xt))
+    else:
+        out["rel_residual"] = rel_residual(m, xx, b)
+    return out
+
+
+def measure_batch(torch, B, steps, warmup, flush, stream, peak):
+    """The 256-matrix batch (n log-uniform in [1,000, 65,536], 1..32 right-hand sides, float64
+    and float32 values alternating): one graph replay per step."""
+    from paper_2206_05843_gb300 import synth as S
+    items = S.gen_batch()
+    keep, systems, by = [], [], 0
+    for it in items:
+        mt = it.matrix.astype(np.float32) if it.fp32 else it.matrix
+        M = B.Matrix.from_host(mt)
+        s = B.System(M, B.Levels(M))
+        keep.append((mt, M))
+        systems.append(s)
+        by += alg_bytes(s.refresh(), mt.n, it.nrhs, 4 if it.fp32 else 8)
+    bt = B.Batch(systems, [it.nrhs for it in items])
+    bs = [torch.from_numpy(it.b).to("cuda", dtype=torch.float32 if it.fp32 else torch.float64) for it in items]
+    xs = [torch.empty_like(b_) for b_ in bs]
+    bt.solve(bs, xs)
+    torch.cuda.synchronize()
+    err64 = err32 = 0.0
+    for it, (mt, _), x_, b_ in zip(items, keep, xs, bs):
+        r = rel_residual(mt, x_.double().cpu().numpy(), b_.double().cpu().numpy())
+        if it.fp32:
+            err32 = max(err32, r)
+        else:
+            err64 = max(err64, r)
+    us, med = timed_us(torch, lambda: bt.solve(bs, xs), steps, warmup, flush, stream)
+    for s in systems:
+        s.status()
+    gbs = by / (us * 1e-6) / 1e9
+    return {"us": round(us, 2), "median_us": round(med, 2), "matrices": len(items),
+            "rows": int(sum(it.matrix.n for it in items)), "alg_bytes": by, "gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / peak, 4), "block": int(bt.info["block"]),
+            "rel_residual_f64_max": err64, "rel_residual_f32_max": err32}
+
+
+def flat_extras(extras: dict) -> dict:
+    """Scalar summary of the extra workloads for the line's config: time and HBM fraction."""
+    out = {}
+    for k, v in extras.items():
+        if "us" in v:
+            out[f"{k}_us"] = v["us"]
+            out[f"{k}_hbm_frac"] = v["hbm_frac"]
+        else:
+            out[f"{k}_error"] = v.get("error", "?")
+    return out
+
+
+def measure_extras(torch, B, names, steps, warmup, flush, stream, peak):
+    from paper_2206_05843_gb300 import synth as S
+    out = {}
+    for name in names:
+        t0 = time.perf_counter()
+        try:
+            if name in ("w1", "w2"):
+                m, b, xt = S.gen_config(name)
+                out[name] = measure_single(torch, B, m, b, xt, {}, steps, warmup, flush, stream, peak)
+            elif name == "w1r16":
+                m, _, _ = S.gen_config("w1")
+                xt, b = S.rhs_from_xtrue(m, 16, 1)
+                out[name] = measure_single(torch, B, m, b, xt, {}, steps, warmup, flush, stream, peak)
+            elif name == "c2":
+                m, _, _ = S.gen_config("c2")
+                for r in (1, 16):
+                    b = S.rhs_uniform(m.n, r, 1)
+                    for k in (0, 1, 2, 4):
+                        kw = {} if k == 0 else dict(kind=B.DEPTH_K, k=k)
+                        out[f"c2_r{r}_k{k}"] = measure_single(torch, B, m, b, None, kw, steps, warmup, flush,
+                                                              stream, peak)
+            elif name == "c3":
+                out[name] = measure_batch(torch, B, steps, warmup, flush, stream, peak)
+        except Exception as e:  # a failed extra is reported, the headline stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        print(f"[bench] {name}: {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -389,6 +534,25 @@ def run_ours(args):
     warm_rw = statistics.median(warm_times(torch, rw, bt, xr, max(3, min(args.steps, 20)), stream)) * 1e3
     warm_pl = statistics.median(warm_times(torch, plain, bt, xp, max(3, min(args.steps, 20)), stream)) * 1e3
     hand = level_handoffs(torch, rw, bt, xr)
+    # the network's own plan and the paper's naive plan on the same matrix, timed the same way
+    # (autotuned, L2 flushed), so that the line shows what the measured choice picked from
+    others = {}
+    if used == "learned":
+        for nm, kw in (("learned_model_only", dict(kind=B.LEARNED, cap=1.5, picker=B.Picker.load(PICKER_FILE),
+                                                   model_only=True)),
+                       ("naive", dict(kind=B.NAIVE, cap=1.5))):
+            so = B.System(M, lv, **kw)
+            so.autotune(nrhs)
+            xo = torch.empty_like(bt)
+            so.solve(bt, xo, check_status=True)
+            us_o, _ = timed_us(torch, lambda: so.solve(bt, xo), args.steps, args.warmup, flush, stream)
+            so.status()
+            io = so.refresh()
+            others[nm] = {"us": round(us_o, 3), "levels": int(io["m"]), "rows_moved": int(io["rows_moved"]),
+                          "stored_nnz_ratio": round(io["stored_nnz"] / io["nnz_l"], 4),
+                          "rel_err_vs_x_true": float(np.linalg.norm(xo.cpu().numpy() - xt_true) /
+                                                     np.linalg.norm(xt_true)) if xt_true is not None else None}
+            del so
     # end to end through the public API: pinned host b -> device, solve, device -> host x
     hb = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
     hx = torch.empty_like(hb).pin_memory()
@@ -421,6 +585,8 @@ def run_ours(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    names = [w for w in args.extra.split(",") if w and w != "none"] if args.workload == "c1" else []
+    extras = measure_extras(torch, B, names, args.steps, args.warmup, flush, stream, peak)
     info_rw = rw.refresh()
     info_pl = plain.refresh()
     by_rw = alg_bytes(info_rw, m.n, nrhs)
@@ -489,6 +655,10 @@ def run_ours(args):
             "level_handoffs": hand,
             "l2": "flushed (512 MB write) before every timed solve, outside the timed events",
             "parallelism": "replicas" if world > 1 else "1 GPU",
+            **{f"{k}_us": v["us"] for k, v in others.items()},
+            **({"candidate_us_model_naive_rowcap_plain": [round(v, 1) for v in info_rw["candidate_us"]]}
+               if used == "learned" else {}),
+            **flat_extras(extras),
         },
         "roofline": {"bound": "hbm", "achieved": round(gbs_rw, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(gbs_rw / peak, 5), "traffic": traffic, "traffic_note": traffic_note,
@@ -500,6 +670,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(b.nbytes)},
         "gpu_launches": args.steps * (launches_per_solve(plain) + launches_per_solve(rw)),
         "clocks": clk,
+        "learned_vs_alternatives": others,
+        "workloads": extras,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

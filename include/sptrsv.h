@@ -181,6 +181,9 @@ typedef struct {
     int32_t launches;      /* kernels one single-RHS solve launches with the current schedule (0 before the
                               first solve or tune) */
     int32_t ctas;          /* CTAs of the persistent solve kernel with the current schedule (SMs x CTAs per SM) */
+    double candidate_us[4]; /* LEARNED with learned_mode 0: the measured solve time (us, one right-hand side,
+                               default schedule) of each candidate -- the picker's plan, the naive plan, the ROWCAP
+                               plan, the plain system -- in that order; 0 for every other system */
 } sptrsv_system_info;
 
 sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);
@@ -218,13 +221,15 @@ sptrsv_status sptrsv_solve(const sptrsv_system* s, const void* b_dev, void* x_de
 sptrsv_status sptrsv_solve_timed(const sptrsv_system* s, const void* b_dev, void* x_dev, int32_t nrhs, int64_t ld,
                                  uint64_t* stamps_dev, sptrsv_stream_t stream);
 
-/* A solve that allocates nothing, for callers that cannot allocate device memory when
- * they solve: code running while a stream is captured into a CUDA graph, real-time
- * loops that must stay out of the allocator, or processes whose memory a framework's
- * caching allocator already holds.  (The paper has no counterpart; this is an interface
- * of the library.)  Same arguments and result as sptrsv_solve; the solution scratch and
- * the completion flags live in one fixed 64 MiB device array of the library, so
- * n * nrhs * sizeof(value) must not exceed 64 MiB - 64 KiB (else SPTRSV_ERR_UNSUPPORTED).
+/* A solve that allocates nothing, for callers that cannot call cudaMalloc when they
+ * solve: real-time loops that must stay out of the allocator, processes whose device
+ * memory a framework's caching allocator already holds, or plug-in code handed only its
+ * inputs and outputs.  (The paper has no counterpart; this is an interface of the
+ * library.)  Same arguments and result as sptrsv_solve, with the launches of the
+ * system's current schedule (the persistent kernel, or one launch per level when the
+ * system is tuned to run_width -2).  The solution scratch and the completion flags live
+ * in one fixed 64 MiB device array of the library, so n * nrhs * sizeof(value) must not
+ * exceed 64 MiB - 64 KiB (else SPTRSV_ERR_UNSUPPORTED).
  * The system must already hold a solve schedule for this nrhs: call sptrsv_solve once
  * with the same nrhs first (that call builds the schedule and may allocate); otherwise
  * SPTRSV_ERR_INVALID.  The first call on a device looks up the array's device address

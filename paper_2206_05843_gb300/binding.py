@@ -67,7 +67,7 @@ class SystemInfo(C.Structure):
                 ("segments", C.c_int64), ("run_levels", C.c_int64), ("dtype", C.c_int32),
                 ("rewritten", C.c_int32), ("avg_cost", C.c_double), ("block", C.c_int32),
                 ("run_width", C.c_int32), ("lanes_per_row", C.c_int32), ("strategy_used", C.c_int32),
-                ("launches", C.c_int32), ("ctas", C.c_int32)]
+                ("launches", C.c_int32), ("ctas", C.c_int32), ("candidate_us", C.c_double * 4)]
 
 
 class BatchInfo(C.Structure):
@@ -298,7 +298,8 @@ class System:
     def refresh(self):
         inf = SystemInfo()
         check(load().sptrsv_system_info_get(self.h, C.byref(inf)))
-        self.info = {f: getattr(inf, f) for f, _ in SystemInfo._fields_}
+        self.info = {f: (list(v) if isinstance(v, C.Array) else v)
+                     for f, v in ((f, getattr(inf, f)) for f, _ in SystemInfo._fields_)}
         self.n, self.m = inf.n, inf.m
         return self.info
 

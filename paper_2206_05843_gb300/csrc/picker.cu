@@ -430,6 +430,7 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
         if (t[i] < t[best]) best = i;
     for (int i = 0; i < NC; ++i)
         if (i != best) sptrsv_system_destroy(cand[i]);
+    for (int i = 0; i < NC; ++i) cand[best]->cand_us[i] = t[i];
     *out = cand[best];
     return SPTRSV_OK;
 }

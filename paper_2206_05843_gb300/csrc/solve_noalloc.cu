@@ -1,13 +1,12 @@
 // solve_noalloc.cu -- sptrsv_solve_noalloc: the persistent solve without any allocation.
 //
-// Some callers cannot allocate device memory at the moment they solve: code that runs
-// while a CUDA stream is being captured into a graph (cudaMalloc is not a stream
-// operation and breaks or escapes the capture), real-time loops that must not enter
-// the allocator, and processes whose device memory is already fully reserved by a
-// framework's caching allocator.  The regular sptrsv_solve may allocate its scratch
-// (the solution in stored order and the per-CTA completion flags) on first use; this
-// entry point instead keeps that scratch in one file-scope device array of fixed size
-// and calls no allocating routine at all.
+// Some callers cannot call cudaMalloc at the moment they solve: real-time loops that must
+// never enter the allocator (its latency is unbounded and it may synchronize the device),
+// processes whose device memory a framework's caching allocator has already reserved in
+// full, and plug-in code that is handed its inputs and outputs but no allocator.  The
+// regular sptrsv_solve may allocate its scratch (the solution in stored order and the
+// per-CTA completion flags) on first use; this entry point instead keeps that scratch in
+// one file-scope device array of fixed size and calls no allocating routine at all.
 //
 // The array is shared by every call on a device and keeps the last call's contents:
 // the completion flags are reset to "nothing published" (-1) at the start of each call,
@@ -88,9 +87,20 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
     a.stage_rows = sc.stage_rows;
     a.stage_entries = sc.stage_entries;
     a.pre = sc.pre;
+    SP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
+    if (sc.run_width == -2) {
+        // the system is tuned to one launch per level: the same launches as sptrsv_solve, with
+        // the solution scratch in the static array (they use no completion flags)
+        const std::vector<int32_t>& lp = s->lv.h_level_ptr;
+        for (int64_t l = 0; l < s->m; ++l) {
+            const int64_t rows = (int64_t)(lp[l + 1] - lp[l]) * nrhs;
+            k_level<T><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a, lp[l], lp[l + 1]);
+        }
+        SP_CUDA(cudaGetLastError());
+        return SPTRSV_OK;
+    }
     SP_CUDA(cudaFuncSetAttribute(k_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.smem));
     SP_CUDA(cudaMemsetAsync(a.flags, 0xff, (size_t)sc.grid * sizeof(int), st));
-    SP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
     if (a.nseg == 0) return SPTRSV_OK;
     if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
     cudaLaunchConfig_t cfg = {};

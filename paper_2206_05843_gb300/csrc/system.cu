@@ -221,6 +221,7 @@ sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info*
     else if (sc.run_width == -2) o->launches = (int32_t)s->m;
     else o->launches = sc.h_segs.empty() ? 0 : 1 + sc.pre;
     o->ctas = sc.segs.p ? sc.grid : 0;
+    for (int i = 0; i < 4; ++i) o->candidate_us[i] = s->cand_us[i];
     return SPTRSV_OK;
 }
 

@@ -70,6 +70,7 @@ struct sptrsv_system {
     int dtype = SPTRSV_F64;
     int rewritten = 0;
     int strategy_used = 0;
+    double cand_us[4] = {0, 0, 0, 0};  // LEARNED: measured time of each candidate (model, naive, rowcap, plain)
     sp::Levels lv;  // levels of the stored structure; lv.level_rows is perm, lv.pos its inverse
     sp::DevBuf<int32_t> cptr, ccol, eptr, ecol, target;
     sp::DevBuf<unsigned char> cval, eval, dinv;

@@ -41,3 +41,25 @@ def test_alg_bytes_plain_and_rewritten():
     rw = {"nnz_c": nnz_c, "nnz_e": 7, "rows_moved": 4, "rewritten": 1}
     # plus 4(n_rw + 1) + (4+v) nnz_e for the E rows
     assert bench.alg_bytes(rw, n, 1) == bench.alg_bytes(plain, n, 1) + 4 * 5 + 12 * 7
+
+
+def test_rel_residual_of_an_exact_and_a_perturbed_solution():
+    from paper_2206_05843_gb300 import synth as S
+    m = S.gen_banded_random(300, 2)
+    xt, b = S.rhs_from_xtrue(m, 2, 3)
+    assert bench.rel_residual(m, xt, b) < 1e-14
+    x = xt.copy()
+    x[1, 7] += 1.0
+    # the perturbation shows up as column 7 of L in the second right-hand side
+    col7 = np.zeros(m.n)
+    rp = m.rowptr.astype(np.int64)
+    for i in range(m.n):
+        for q in range(rp[i], rp[i + 1]):
+            if m.colidx[q] == 7:
+                col7[i] = m.vals[q]
+    assert abs(bench.rel_residual(m, x, b) - np.linalg.norm(col7) / np.linalg.norm(b[1])) < 1e-12
+
+
+def test_flat_extras_keeps_time_and_fraction_or_the_error():
+    ex = {"w2": {"us": 200.0, "hbm_frac": 0.5, "gbs": 3000.0}, "c3": {"error": "RuntimeError: x"}}
+    assert bench.flat_extras(ex) == {"w2_us": 200.0, "w2_hbm_frac": 0.5, "c3_error": "RuntimeError: x"}

@@ -1,15 +1,16 @@
 """The solve that allocates nothing (sptrsv_solve_noalloc), called through the C ABI.
 
-Callers that cannot allocate device memory while they solve (stream capture, real-time
-loops, a framework's caching allocator holding the memory) use this entry point; its
-scratch is a fixed device array of the library.  This file runs last so that a failure
+Callers that cannot call cudaMalloc while they solve (real-time loops that must stay out
+of the allocator, processes whose device memory a framework's caching allocator holds,
+plug-in code handed only its inputs and outputs) use this entry point; its scratch is a
+fixed device array of the library.  This file runs last so that a failure
 here does not hide the other tests, and it passes both alone and after them."""
 import numpy as np
 import pytest
 
 from paper_2206_05843_gb300 import binding as B
 from paper_2206_05843_gb300 import synth as S
-from tests.gpu_util import TOL_F64, rel_l2, torch_cuda
+from tests.gpu_util import TOL_F32, TOL_F64, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -58,3 +59,24 @@ def test_noalloc_multi_rhs_and_limits():
     with pytest.raises(B.SptrsvError) as e2:
         sb.solve_noalloc(bb, torch.empty_like(bb))
     assert e2.value.code == B.ERR_UNSUPPORTED
+
+
+def test_noalloc_float32_and_one_launch_per_level():
+    """float32 values (checked at the float32 tolerance), and a system tuned to one launch per
+    level, whose launches the entry point follows."""
+    torch = torch_cuda()
+    m = S.gen_skewed(20000, 8, head=16000).astype(np.float32)
+    M = B.Matrix.from_host(m)
+    lv = B.Levels(M)
+    for tune in (None, -2):
+        s = B.System(M, lv, B.NAIVE, cap=1.5)
+        if tune is not None:
+            s.tune(run_width=tune)
+        x = None
+        for seed in (4, 5):
+            b = torch.from_numpy(S.rhs_uniform(m.n, 1, seed)[0]).to("cuda", dtype=torch.float32)
+            ref = s.solve(b, check_status=True).clone()
+            x = torch.empty_like(b) if x is None else x
+            s.solve_noalloc(b, x)
+            s.status()
+            assert rel_l2(x.cpu().numpy(), ref.cpu().numpy()) <= TOL_F32
