@@ -184,6 +184,10 @@ typedef struct {
     double candidate_us[4]; /* LEARNED with learned_mode 0: the measured solve time (us, one right-hand side,
                                default schedule) of each candidate -- the picker's plan, the naive plan, the ROWCAP
                                plan, the plain system -- in that order; 0 for every other system */
+    int32_t cluster;       /* CTAs per thread-block cluster of the persistent solve (1: no CLUSTER segments) */
+    int32_t cluster_setting; /* the system's cluster knob (0 automatic, 1 off, 2..16 CTAs) */
+    int64_t cluster_levels; /* levels executed in CLUSTER segments */
+    int64_t cluster_rows;  /* the system's widest-cluster-level knob (0 automatic) */
 } sptrsv_system_info;
 
 sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);
@@ -266,6 +270,12 @@ sptrsv_status sptrsv_debug_set_wait(sptrsv_system* s, int64_t withhold_segment, 
  * kernel, widest level executed inside a single-CTA run (-1: no runs; -2: no persistent
  * kernel at all, one launch of a row-per-thread kernel per level), lanes per row. */
 sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_width, int32_t lanes_per_row);
+
+/* Cluster knobs of one system: levels wider than a single-CTA run and at most cluster_rows rows
+ * (0: automatic, 16384) run as CLUSTER segments on the `cluster` CTAs of one thread-block cluster
+ * (2..16; 0: automatic, 16; 1: no clusters), one cluster barrier per level instead of a
+ * device-wide handoff.  Negative values keep the current setting.  No stream work. */
+sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows);
 
 /* Autotuner: times candidate solves (b = 0) over lanes per row and the widest level
  * executed inside a single-CTA run, keeps the fastest for nrhs right-hand sides and

@@ -29,7 +29,8 @@ EXPORTED = [
     "sptrsv_levels_destroy", "sptrsv_system_plain", "sptrsv_rewrite", "sptrsv_system_info_get",
     "sptrsv_system_export", "sptrsv_system_destroy", "sptrsv_solve", "sptrsv_solve_timed", "sptrsv_solve_status",
     "sptrsv_solve_noalloc", "sptrsv_system_autotune", "sptrsv_upper_to_lower", "sptrsv_system_reverse_rows",
-    "sptrsv_debug_set_wait", "sptrsv_system_tune", "sptrsv_batch_create", "sptrsv_batch_solve",
+    "sptrsv_debug_set_wait", "sptrsv_system_tune", "sptrsv_system_tune_cluster", "sptrsv_batch_create",
+    "sptrsv_batch_solve",
     "sptrsv_batch_info_get", "sptrsv_batch_destroy", "sptrsv_picker_create", "sptrsv_picker_destroy",
     "sptrsv_picker_get_params", "sptrsv_picker_set_params", "sptrsv_picker_set_norm", "sptrsv_picker_save",
     "sptrsv_picker_load", "sptrsv_picker_features", "sptrsv_picker_infer", "sptrsv_picker_grad",
@@ -67,7 +68,9 @@ class SystemInfo(C.Structure):
                 ("segments", C.c_int64), ("run_levels", C.c_int64), ("dtype", C.c_int32),
                 ("rewritten", C.c_int32), ("avg_cost", C.c_double), ("block", C.c_int32),
                 ("run_width", C.c_int32), ("lanes_per_row", C.c_int32), ("strategy_used", C.c_int32),
-                ("launches", C.c_int32), ("ctas", C.c_int32), ("candidate_us", C.c_double * 4)]
+                ("launches", C.c_int32), ("ctas", C.c_int32), ("candidate_us", C.c_double * 4),
+                ("cluster", C.c_int32), ("cluster_setting", C.c_int32), ("cluster_levels", C.c_int64),
+                ("cluster_rows", C.c_int64)]
 
 
 class BatchInfo(C.Structure):
@@ -106,6 +109,7 @@ def load():
             "sptrsv_debug_set_wait": [vp, i64, i64],
             "sptrsv_debug_run_blocks": [vp, i64, vp, i32, i32, i32, vp, i64, vp, vp],
             "sptrsv_system_tune": [vp, i32, i32, i32],
+            "sptrsv_system_tune_cluster": [vp, i32, i64],
             "sptrsv_system_autotune": [vp, i32, vp, vp],
             "sptrsv_upper_to_lower": [vp, vp, vp, vp, vp],
             "sptrsv_system_reverse_rows": [vp, vp],
@@ -308,6 +312,10 @@ class System:
 
     def tune(self, block=0, run_width=0, lanes_per_row=0):
         check(load().sptrsv_system_tune(self.h, block, run_width, lanes_per_row))
+
+    def tune_cluster(self, cluster=-1, cluster_rows=-1):
+        """CTAs per cluster for mid-width levels (0 automatic, 1 none) and the widest such level."""
+        check(load().sptrsv_system_tune_cluster(self.h, cluster, cluster_rows))
 
     def autotune(self, nrhs=1) -> float:
         """Times candidate schedules and keeps the fastest; returns its time in us."""

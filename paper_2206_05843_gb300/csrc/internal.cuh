@@ -111,6 +111,10 @@ __device__ __forceinline__ int ld_volatile(const int* p) {
     asm volatile("ld.volatile.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// Cluster barrier, split: arrive (release: this thread's earlier writes become visible to the
+// cluster) and wait (acquire).  Every thread of every CTA of the cluster must take both, in order.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -52,6 +52,7 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     a.stage_rows = sc.stage_rows;
     a.stage_entries = sc.stage_entries;
     a.pre = sc.pre;
+    a.csize = sc.csize;
 
     SP_CUDA(cudaMemsetAsync(s->flags.p, 0xff, (size_t)sc.grid * sizeof(int), st));
     SP_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
@@ -68,17 +69,39 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     }
     if (a.nseg == 0) return SPTRSV_OK;
     if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)sc.grid);
-    cfg.blockDim = dim3((unsigned)sc.block);
-    cfg.dynamicSmemBytes = sc.smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident: waits always make progress
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    SP_CUDA(cudaLaunchKernelEx(&cfg, k_solve<T>, a));
+    SP_CUDA(launch_k_solve<T>(a, sc.grid, sc.block, sc.smem, sc.csize, st));
+    return SPTRSV_OK;
+}
+
+// CTAs of the persistent kernel that can be co-resident with the given block, shared memory and
+// cluster size (cluster size 1: no clusters); 0 when the configuration does not fit.
+template <typename T>
+sptrsv_status solve_capacity(int block, size_t smem, int csize, int64_t* ctas) {
+    *ctas = 0;
+    SP_CUDA(k_solve_attrs<T>(smem, csize));
+    if (csize <= 1) {
+        int occ = 0;
+        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve<T, false>, block, smem));
+        *ctas = (int64_t)device_sm_count() * occ;
+        return SPTRSV_OK;
+    }
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3((unsigned)csize);
+    q.blockDim = dim3((unsigned)block);
+    q.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    q.attrs = at;
+    q.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_solve<T, true>, &q) != cudaSuccess) {
+        cudaGetLastError();  // a cluster size the device cannot place: no clusters
+        ncl = 0;
+    }
+    *ctas = (int64_t)ncl * csize;
     return SPTRSV_OK;
 }
 
@@ -206,7 +229,8 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
         set_error("lanes per row must be a power of two <= 32");
         return SPTRSV_ERR_INVALID;
     }
-    if (sc.nrhs == nrhs && sc.lpr == lpr && sc.block == block && sc.run_width == s->run_width && sc.segs.p)
+    if (sc.nrhs == nrhs && sc.lpr == lpr && sc.block == block && sc.run_width == s->run_width &&
+        sc.cluster == s->cluster && sc.cluster_rows == s->cluster_rows && sc.segs.p)
         return SPTRSV_OK;
     const int ngroups = block / lpr;
     // shared memory: two staging buffers + an x ring of at least twice the staged rows
@@ -229,27 +253,67 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     int sms = device_sm_count();
     // occupancy decides the number of CTAs that WIDE levels can be split over
     size_t smem = run_smem_bytes(vb, nrhs, RunGeom{ring_rows, stage_rows, stage_entries});
-    int occ = 0;
+    int64_t gplain = 0, gcl = 0;
+    int csize = s->cluster == 1 ? 1 : (s->cluster > 1 ? std::min(16, s->cluster) : CLUSTER_DEFAULT);
+    const int64_t cl_rows = s->cluster_rows > 0 ? s->cluster_rows : CLUSTER_ROWS_DEFAULT;
     if (s->dtype == SPTRSV_F64) {
-        SP_CUDA(cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve<double>, block, smem));
+        SP_TRY(solve_capacity<double>(block, smem, 1, &gplain));
+        if (csize > 1) SP_TRY(solve_capacity<double>(block, smem, csize, &gcl));
     } else {
-        SP_CUDA(cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve<float>, block, smem));
+        SP_TRY(solve_capacity<float>(block, smem, 1, &gplain));
+        if (csize > 1) SP_TRY(solve_capacity<float>(block, smem, csize, &gcl));
     }
-    if (occ < 1) {
+    if (gplain < 1) {
         set_error("solve kernel does not fit an SM with block %d and %zu bytes of shared memory", block, smem);
         return SPTRSV_ERR_UNSUPPORTED;
     }
-    const int64_t gmax = (int64_t)sms * occ;
+    if (gcl < csize) csize = 1;
     auto thin = [&](int64_t l) {
         return lp[l + 1] - lp[l] <= run_width && (int64_t)hcptr[lp[l + 1]] - hcptr[lp[l]] <= stage_entries;
     };
+    // level kinds: 0 thin (single-CTA runs), 1 mid-width (cluster levels), 2 wide (all CTAs)
+    std::vector<unsigned char> kind(m);
+    bool any_mid = false;
+    for (int64_t l = 0; l < m; ++l) {
+        kind[l] = thin(l) ? 0 : (csize > 1 && lp[l + 1] - lp[l] <= cl_rows ? 1 : 2);
+        any_mid |= kind[l] == 1;
+    }
+    if (any_mid) {
+        // short stretches of thin levels next to cluster levels become cluster levels: a cluster
+        // barrier per level costs less than entering and leaving a staged single-CTA run
+        int64_t l = 0;
+        while (l < m) {
+            if (kind[l] != 0) { ++l; continue; }
+            int64_t l1 = l;
+            while (l1 < m && kind[l1] == 0) ++l1;
+            const bool next_to_mid = (l > 0 && kind[l - 1] == 1) || (l1 < m && kind[l1] == 1);
+            if (l1 - l < CLUSTER_RUN_MIN && next_to_mid)
+                for (int64_t q = l; q < l1; ++q) kind[q] = 1;
+            l = l1;
+        }
+    } else {
+        csize = 1;
+    }
+    const int64_t gmax = csize > 1 ? gcl : gplain;
+    sc.cluster_levels = 0;
     int64_t l = 0;
     while (l < m) {
-        if (thin(l)) {
+        if (kind[l] == 1) {
+            int64_t l1 = l, ents = 0;
+            while (l1 < m && kind[l1] == 1) ++l1;
+            ents = (int64_t)hcptr[lp[l1]] - hcptr[lp[l]];
+            const int64_t rows = lp[l1] - lp[l];
+            // lanes per row of the segment: two for single right-hand sides of 4 or more coefficients
+            const int wl = (nrhs == 1 && lpr == 1 && ents >= 4 * rows) ? 2 : lpr;
+            sc.h_segs.push_back(make_int4(SEG_CLUSTER | (wl == lpr ? 0 : wl << SEG_LPR_SHIFT), (int)l, (int)l1, csize));
+            sc.cluster_levels += l1 - l;
+            max_parts = std::max<int64_t>(max_parts, csize);
+            l = l1;
+            continue;
+        }
+        if (kind[l] == 0) {
             int64_t l1 = l;
-            while (l1 < m && thin(l1)) ++l1;
+            while (l1 < m && kind[l1] == 0) ++l1;
             int blk0 = (int)sc.h_blocks.size();
             if (build_run_blocks(lp.data(), hcptr.data(), l, l1, stage_rows, stage_entries, lpr, nrhs,
                                  fast_rec_capacity(vb, RunGeom{ring_rows, stage_rows, stage_entries}),
@@ -276,6 +340,20 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
             ++l;
         }
     }
+    // cluster regions: maximal stretches of RUN and CLUSTER segments that hold a CLUSTER segment
+    for (size_t i = 0; i < sc.h_segs.size();) {
+        if ((sc.h_segs[i].x & SEG_TYPE_MASK) == SEG_WIDE) { ++i; continue; }
+        size_t j = i;
+        bool has_cl = false;
+        while (j < sc.h_segs.size() && (sc.h_segs[j].x & SEG_TYPE_MASK) != SEG_WIDE)
+            has_cl |= (sc.h_segs[j++].x & SEG_TYPE_MASK) == SEG_CLUSTER;
+        if (has_cl) {
+            for (size_t q = i; q < j; ++q) sc.h_segs[q].x |= SEG_REGION;
+            sc.h_segs[i].x |= SEG_FIRST;
+            sc.h_segs[j - 1].x |= SEG_LAST;
+        }
+        i = j;
+    }
     // rewritten rows in thin levels: their b-parts (E rows) are computed up front by every
     // CTA, so that staging reads one value per row instead of walking the E row
     sc.pre = s->nnz_e > 0 && !sc.h_blocks.empty() && nrhs * (int64_t)vb <= 64 ? 1 : 0;
@@ -287,6 +365,10 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
         SP_CUDA(cudaMemcpy(sc.segs.p, sc.h_segs.data(), sc.h_segs.size() * sizeof(int4), cudaMemcpyHostToDevice));
     SP_CUDA(cudaMemcpy(sc.blocks.p, sc.h_blocks.data(), sc.h_blocks.size() * sizeof(int4), cudaMemcpyHostToDevice));
     sc.grid = (int)std::min<int64_t>(gmax, max_parts);
+    if (csize > 1) sc.grid = (int)std::min<int64_t>(gmax, (std::max<int64_t>(max_parts, csize) + csize - 1) / csize * csize);
+    sc.csize = csize;
+    sc.cluster = s->cluster;
+    sc.cluster_rows = s->cluster_rows;
     sc.nrhs = nrhs;
     sc.lpr = lpr;
     sc.block = block;
@@ -328,6 +410,8 @@ struct TuneKey {
 struct TuneVal {
     int block, run_width, lpr;
     double us;
+    int cluster = 0;
+    int64_t cluster_rows = 0;
 };
 std::mutex g_stune_mu;
 std::map<TuneKey, TuneVal> g_stune_cache;
@@ -351,6 +435,8 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
             s->block = f->second.block;
             s->run_width = f->second.run_width;
             s->lpr = f->second.lpr;
+            s->cluster = f->second.cluster;
+            s->cluster_rows = f->second.cluster_rows;
             if (best_us) *best_us = f->second.us;
             return prepare_schedule(s, nrhs);
         }
@@ -375,32 +461,60 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
     SP_CUDA(cudaEventCreate(&e0));
     SP_CUDA(cudaEventCreate(&e1));
     TuneVal best{512, 0, 0, 1e300};
-    const int old_block = s->block, old_rw = s->run_width, old_lpr = s->lpr;
+    const int old_block = s->block, old_rw = s->run_width, old_lpr = s->lpr, old_cl = s->cluster;
+    const int64_t old_clr = s->cluster_rows;
     sptrsv_status rc = SPTRSV_OK;
+    // best of 3 timed solves of the current settings, in microseconds
+    auto time_current = [&](double* us) -> sptrsv_status {
+        s->sched.nrhs = -1;
+        SP_TRY(enqueue_solve(s, b.p, x.p, nrhs, s->n, nullptr, st));
+        float bestms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            SP_TRY(enqueue_solve(s, b.p, x.p, nrhs, s->n, nullptr, st));
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            bestms = std::min(bestms, ms);
+        }
+        *us = bestms * 1e3;
+        return SPTRSV_OK;
+    };
+    // lanes per row x widest single-CTA level x the cluster that runs mid-width levels (none, 16
+    // or 8 CTAs); then the widest cluster level for the best of those
+    const int cls[][2] = {{1, 0}, {16, 16384}, {8, 16384}};
     for (int lpr : lprs) {
         for (int rw : widths) {
             if (rw == -2 && lpr != lprs[0]) continue;
-            s->block = 512;
-            s->run_width = rw;
-            s->lpr = lpr;
-            s->sched.nrhs = -1;
-            rc = enqueue_solve(s, b.p, x.p, nrhs, s->n, nullptr, st);
-            if (rc != SPTRSV_OK) break;
-            float bestms = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, st);
-                rc = enqueue_solve(s, b.p, x.p, nrhs, s->n, nullptr, st);
-                cudaEventRecord(e1, st);
+            for (const auto& c : cls) {
+                if (rw == -2 && c[0] != 1) continue;  // one launch per level has no clusters
+                s->block = 512;
+                s->run_width = rw;
+                s->lpr = lpr;
+                s->cluster = c[0];
+                s->cluster_rows = c[1];
+                double us = 0;
+                rc = time_current(&us);
                 if (rc != SPTRSV_OK) break;
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                bestms = std::min(bestms, ms);
+                if (us < best.us) best = TuneVal{512, rw, lpr, us, c[0], c[1]};
             }
             if (rc != SPTRSV_OK) break;
-            if (bestms * 1e3 < best.us) best = TuneVal{512, rw, lpr, bestms * 1e3};
         }
         if (rc != SPTRSV_OK) break;
+    }
+    if (rc == SPTRSV_OK && best.cluster > 1) {
+        s->block = best.block;
+        s->run_width = best.run_width;
+        s->lpr = best.lpr;
+        s->cluster = best.cluster;
+        for (int64_t rows : {(int64_t)4096, (int64_t)65536}) {
+            s->cluster_rows = rows;
+            double us = 0;
+            rc = time_current(&us);
+            if (rc != SPTRSV_OK) break;
+            if (us < best.us) best = TuneVal{best.block, best.run_width, best.lpr, us, best.cluster, rows};
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -408,6 +522,8 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         s->block = old_block;
         s->run_width = old_rw;
         s->lpr = old_lpr;
+        s->cluster = old_cl;
+        s->cluster_rows = old_clr;
         s->sched.nrhs = -1;
         return rc;
     }
@@ -415,6 +531,8 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
     s->block = best.block;
     s->run_width = best.run_width;
     s->lpr = best.lpr;
+    s->cluster = best.cluster;
+    s->cluster_rows = best.cluster_rows;
     s->sched.nrhs = -1;
     {
         std::lock_guard<std::mutex> lk(g_stune_mu);

@@ -23,7 +23,7 @@ template <typename T>
 __device__ bool wait_segment(const SolveArgs<T>& a, int s) {
     if (s < 0) return true;
     int4 sg = a.segs[s];
-    int parts = (sg.x & SEG_TYPE_MASK) == SEG_WIDE ? sg.w : 1;
+    int parts = (sg.x & SEG_TYPE_MASK) == SEG_RUN ? 1 : sg.w;
     bool failed = false;
     for (int t = threadIdx.x; t < parts && !failed; t += blockDim.x) {
         const int* f = a.flags + t;
@@ -66,9 +66,9 @@ __device__ __forceinline__ T bpart(const SolveArgs<T>& a, int64_t p, int32_t row
 
 // Wide level, several right-hand sides or several lanes per row: the first row of each
 // thread is prepared (coefficients in registers, b-part) before the wait.
-template <typename T>
+template <typename T, typename WaitFn>
 __device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ngroups, int grp, int64_t my0,
-                                  int64_t my1, int s) {
+                                  int64_t my1, WaitFn wait) {
     const int nrhs = a.nrhs;
     const int64_t pf = my0 + grp;
     const bool act0 = pf < my1;
@@ -86,7 +86,7 @@ __device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ng
         pval[u] = ok ? a.cval[q] : T(0);
     }
     if (act0 && single && ln.rl < nrhs) pre = bpart(a, pf, row0, ln.rl, ln);
-    if (!wait_segment(a, s - 1)) return false;
+    if (!wait()) return false;
     for (int64_t base = my0; base < my1; base += ngroups) {
         const int64_t p = base + grp;
         const bool act = p < my1;
@@ -174,8 +174,8 @@ __device__ __forceinline__ T row_1rhs(const SolveArgs<T>& a, int64_t p, int32_t 
     return acc;
 }
 
-template <typename T>
-__device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, int s) {
+template <typename T, typename WaitFn>
+__device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, WaitFn wait) {
     const int64_t pf = my0 + threadIdx.x;
     const bool act0 = pf < my1;
     const int32_t row0 = act0 ? __ldcs(a.perm + pf) : 0;
@@ -189,7 +189,7 @@ __device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, 
         pcol[u] = ok ? __ldcs(a.ccol + f0 + u) : 0;
         pval[u] = ok ? __ldcs(a.cval + f0 + u) : T(0);
     }
-    if (!wait_segment(a, s - 1)) return false;
+    if (!wait()) return false;
     if (act0) {
         T xv[PF];
 #pragma unroll
@@ -302,46 +302,153 @@ __global__ void k_stamp(unsigned long long* stamps, int64_t l) {
 // the kernel
 // ---------------------------------------------------------------------------------
 
-template <typename T>
+// the rows [my0, my1) of one level with lanes-per-row wl (0: the schedule's), `wait` taken after the
+// first row's independent data is in registers
+template <typename T, typename WaitFn>
+__device__ __forceinline__ bool level_rows(const SolveArgs<T>& a, const Lanes& ln, int wl, int64_t my0, int64_t my1,
+                                           WaitFn wait) {
+    if (wl <= 0) wl = a.lpr;
+    if (a.nrhs == 1 && wl == 1) return wide_rows_1rhs(a, my0, my1, wait);
+    if (wl == a.lpr) return wide_rows_general(a, ln, (int)blockDim.x / a.lpr, (int)threadIdx.x / a.lpr, my0, my1, wait);
+    const Lanes lw = make_lanes(wl, a.nrhs);
+    return wide_rows_general(a, lw, (int)blockDim.x / wl, (int)threadIdx.x / wl, my0, my1, wait);
+}
+
+// A CTA whose bounded wait ran out ("dead": the status word is set) does no more work and no more
+// flag waits, and publishes nothing, so that the CTAs waiting on it run out too; inside a cluster
+// region it still takes every cluster barrier, so that no CTA of its cluster waits on it forever.
+// No CTA returns early.
+template <typename T, bool CL>
 __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int nrhs = a.nrhs;
     const Lanes ln = make_lanes(a.lpr, nrhs);
-    const int ngroups = blockDim.x / a.lpr;
-    const int grp = threadIdx.x / a.lpr;
     const int me = blockIdx.x;
-
-    for (int s = 0; s < a.nseg; ++s) {
-        const int4 sg = a.segs[s];
-        if ((sg.x & SEG_TYPE_MASK) == SEG_WIDE) {
-            if (me >= sg.w) continue;
-            const int l = sg.y;
-            const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
-            const int64_t my0 = p0 + (int64_t)me * sg.z;
-            const int64_t my1 = min(p1, my0 + (int64_t)sg.z);
-            const int wl = (sg.x >> SEG_LPR_SHIFT) > 0 ? (sg.x >> SEG_LPR_SHIFT) : a.lpr;
-            if (nrhs == 1 && wl == 1) {
-                if (!wide_rows_1rhs(a, my0, my1, s)) return;
-            } else if (wl == a.lpr) {
-                if (!wide_rows_general(a, ln, ngroups, grp, my0, my1, s)) return;
+    if constexpr (!CL) {
+        // no CLUSTER segments: a CTA whose bounded wait runs out returns
+        for (int s = 0; s < a.nseg; ++s) {
+            const int4 sg = a.segs[s];
+            const int wl = (sg.x >> SEG_LPR_SHIFT) & SEG_LPR_MASK;
+            if ((sg.x & SEG_TYPE_MASK) == SEG_WIDE) {
+                if (me >= sg.w) continue;
+                const int l = sg.y;
+                const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
+                const int64_t my0 = p0 + (int64_t)me * sg.z;
+                const int64_t my1 = min(p1, my0 + (int64_t)sg.z);
+                if (!level_rows(a, ln, wl, my0, my1, [&]() { return wait_segment(a, s - 1); })) return;
+                publish(a, s);
+                if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
             } else {
-                const Lanes lw = make_lanes(wl, nrhs);
-                if (!wide_rows_general(a, lw, (int)blockDim.x / wl, (int)threadIdx.x / wl, my0, my1, s)) return;
+                if (me != 0) continue;
+                SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval,
+                             a.dinv, a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp,
+                             a.pre ? a.xp : nullptr};
+                auto wait = [&]() { return wait_segment(a, s - 1); };
+                if (!run_blocks(v, smem, RunGeom{a.ring_rows, a.stage_rows, a.stage_entries}, ln, a.blocks, sg.y,
+                                sg.z, wait, a.stamps))
+                    return;
+                publish(a, s);
             }
-            publish(a, s);
-            if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
-        } else {
-            if (me != 0) continue;
-            SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval,
-                         a.dinv, a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp,
-                         a.pre ? a.xp : nullptr};
-            auto wait = [&]() { return wait_segment(a, s - 1); };
-            if (!run_blocks(v, smem, RunGeom{a.ring_rows, a.stage_rows, a.stage_entries}, ln, a.blocks, sg.y, sg.z,
-                            wait, a.stamps))
-                return;
-            publish(a, s);
+        }
+    } else {
+        const bool cluster0 = me < a.csize;  // cluster 0: CTAs 0 .. csize-1 of the 1-D grid
+        bool dead = false;
+        for (int s = 0; s < a.nseg; ++s) {
+            const int4 sg = a.segs[s];
+            const int type = sg.x & SEG_TYPE_MASK;
+            const int wl = (sg.x >> SEG_LPR_SHIFT) & SEG_LPR_MASK;
+            const bool region = CL && (sg.x & SEG_REGION) != 0;
+            const bool first = (sg.x & SEG_FIRST) != 0, last = (sg.x & SEG_LAST) != 0;
+            if (region ? !cluster0 : (dead || (type == SEG_WIDE ? me >= sg.w : me != 0))) continue;
+            if (type == SEG_RUN) {
+                // entry: the cluster barrier of the previous segment inside a region, else its flags
+                const bool barrier_entry = region && !first;
+                const bool was_dead = dead;
+                auto w = [&a, s, barrier_entry, was_dead]() -> bool {
+                    if (barrier_entry) {
+                        cluster_wait();
+                        return !was_dead;
+                    }
+                    return was_dead ? false : wait_segment(a, s - 1);
+                };
+                bool ok;
+                if (me == 0) {
+                    SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval,
+                                 a.dinv, a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp,
+                                 a.pre ? a.xp : nullptr};
+                    ok = was_dead ? (w(), false)
+                                  : run_blocks(v, smem, RunGeom{a.ring_rows, a.stage_rows, a.stage_entries}, ln, a.blocks,
+                                               sg.y, sg.z, w, a.stamps);
+                } else {
+                    ok = barrier_entry ? w() : !was_dead;  // other CTAs of the cluster: the barrier only
+                }
+                if (!ok) dead = true;
+                if (region && !last) cluster_arrive();
+            } else {
+                // WIDE: one level over CTAs 0..parts-1; CLUSTER: levels [y, z), each over the cluster
+                const int la = sg.y, lb = CL && type == SEG_CLUSTER ? sg.z : sg.y + 1;
+                for (int l = la; l < lb; ++l) {
+                    const bool barrier_entry = l != la || (region && !first);
+                    const bool was_dead = dead;
+                    auto w = [&a, s, barrier_entry, was_dead]() -> bool {
+                        if (barrier_entry) {
+                            cluster_wait();
+                            return !was_dead;
+                        }
+                        return was_dead ? false : wait_segment(a, s - 1);
+                    };
+                    const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
+                    const int chunk = type == SEG_WIDE ? sg.z : ((int)(p1 - p0) + a.csize - 1) / a.csize;
+                    const int64_t my0 = min(p1, p0 + (int64_t)me * chunk), my1 = min(p1, my0 + chunk);
+                    const bool ok = was_dead ? (w(), false) : level_rows(a, ln, wl, my0, my1, w);
+                    if (!ok) dead = true;
+                    else if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
+                    if (region && (l + 1 < lb || !last)) cluster_arrive();
+                }
+            }
+            // completion flags: outside regions after every segment, else after the region's last one
+            // (by the CTAs that worked on it: all of a CLUSTER segment, CTA 0 of a RUN)
+            if (!dead && (!region || last) && (type != SEG_RUN || me == 0)) publish(a, s);
         }
     }
+}
+
+// Kernel attributes of the k_solve instantiation a launch with csize CTAs per cluster uses
+template <typename T>
+cudaError_t k_solve_attrs(size_t smem, int csize) {
+    if (csize > 1) {
+        cudaError_t e = cudaFuncSetAttribute(k_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && csize > 8)
+            e = cudaFuncSetAttribute(k_solve<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return e;
+    }
+    return cudaFuncSetAttribute(k_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Launches k_solve for a prepared schedule: cooperative (all CTAs co-resident, so every bounded
+// wait can succeed), and with the schedule's cluster size when it has CLUSTER segments.
+template <typename T>
+cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t smem, int csize, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    int na = 1;
+    if (csize > 1) {
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = (unsigned)csize;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        na = 2;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    if (csize > 1) return cudaLaunchKernelEx(&cfg, k_solve<T, true>, a);
+    return cudaLaunchKernelEx(&cfg, k_solve<T, false>, a);
 }
 
 }  // namespace

@@ -87,6 +87,7 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
     a.stage_rows = sc.stage_rows;
     a.stage_entries = sc.stage_entries;
     a.pre = sc.pre;
+    a.csize = sc.csize;
     SP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
     if (sc.run_width == -2) {
         // the system is tuned to one launch per level: the same launches as sptrsv_solve, with
@@ -99,21 +100,11 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
         SP_CUDA(cudaGetLastError());
         return SPTRSV_OK;
     }
-    SP_CUDA(cudaFuncSetAttribute(k_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc.smem));
+    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize));
     SP_CUDA(cudaMemsetAsync(a.flags, 0xff, (size_t)sc.grid * sizeof(int), st));
     if (a.nseg == 0) return SPTRSV_OK;
     if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)sc.grid);
-    cfg.blockDim = dim3((unsigned)sc.block);
-    cfg.dynamicSmemBytes = sc.smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    SP_CUDA(cudaLaunchKernelEx(&cfg, k_solve<T>, a));
+    SP_CUDA(launch_k_solve<T>(a, sc.grid, sc.block, sc.smem, sc.csize, st));
     return SPTRSV_OK;
 }
 

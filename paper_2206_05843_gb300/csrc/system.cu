@@ -222,6 +222,10 @@ sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info*
     else o->launches = sc.h_segs.empty() ? 0 : 1 + sc.pre;
     o->ctas = sc.segs.p ? sc.grid : 0;
     for (int i = 0; i < 4; ++i) o->candidate_us[i] = s->cand_us[i];
+    o->cluster = sc.segs.p ? sc.csize : 1;
+    o->cluster_setting = s->cluster;
+    o->cluster_levels = sc.segs.p ? sc.cluster_levels : 0;
+    o->cluster_rows = s->cluster_rows;
     return SPTRSV_OK;
 }
 
@@ -304,6 +308,15 @@ sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_wi
     if (block) s->block = block;
     if (run_width) s->run_width = run_width;
     if (lanes_per_row) s->lpr = lanes_per_row;
+    s->sched.nrhs = -1;  // rebuild on the next solve
+    return SPTRSV_OK;
+}
+
+sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows) {
+    if (!s) { set_error("system_tune_cluster: null system"); return SPTRSV_ERR_INVALID; }
+    if (cluster > 16) { set_error("system_tune_cluster: at most 16 CTAs per cluster"); return SPTRSV_ERR_INVALID; }
+    if (cluster >= 0) s->cluster = cluster;
+    if (cluster_rows >= 0) s->cluster_rows = cluster_rows;
     s->sched.nrhs = -1;  // rebuild on the next solve
     return SPTRSV_OK;
 }

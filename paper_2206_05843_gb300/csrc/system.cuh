@@ -5,23 +5,42 @@
 
 namespace sp {
 
-// WIDE: one level over CTAs 0..w-1; RUN: staged blocks [y, z) on CTA 0.  The type is in the low
-// byte of a segment's x; a WIDE segment keeps its lanes per row above it (0: the schedule's)
-enum SegType : int { SEG_WIDE = 0, SEG_RUN = 1 };
-constexpr int SEG_TYPE_MASK = 0xff, SEG_LPR_SHIFT = 8;
+// WIDE: one level over CTAs 0..w-1; RUN: staged blocks [y, z) on CTA 0; CLUSTER: levels [y, z), each
+// split over the w CTAs of cluster 0.  The type is in the low byte of a segment's x; a WIDE or CLUSTER
+// segment keeps its lanes per row in the next byte (0: the schedule's).
+enum SegType : int { SEG_WIDE = 0, SEG_RUN = 1, SEG_CLUSTER = 2 };
+constexpr int SEG_TYPE_MASK = 0xff, SEG_LPR_SHIFT = 8, SEG_LPR_MASK = 0xff;
+// A cluster region: consecutive RUN and CLUSTER segments that the CTAs of cluster 0 execute with
+// cluster barriers (barrier.cluster, ~0.4 us) between them instead of device-wide completion flags.
+// Every segment of a region carries SEG_REGION; the first (SEG_FIRST) is entered through the flags
+// of the segment before it, the last (SEG_LAST) publishes the flags for the segment after it.
+constexpr int SEG_REGION = 1 << 16, SEG_FIRST = 1 << 17, SEG_LAST = 1 << 18;
 
 // rows a ROWCAP target holds by default: the lanes of one warp, the fast executor's level width
 constexpr int ROWCAP_DEFAULT_ROWS = 32;
 
+// CLUSTER segments (automatic settings): levels wider than a single-CTA run and at most
+// CLUSTER_ROWS_DEFAULT rows run on a cluster of CLUSTER_DEFAULT CTAs; a stretch of fewer than
+// CLUSTER_RUN_MIN thin levels next to such levels joins them
+constexpr int CLUSTER_DEFAULT = 16;
+constexpr int64_t CLUSTER_ROWS_DEFAULT = 16384;
+constexpr int CLUSTER_RUN_MIN = 4;
+
 // A segment of the persistent solve.  WIDE: one level split over CTAs 0..parts-1.
 // RUN: consecutive thin levels executed by CTA 0 alone, staged block by block.
-// int4 layout: {type, a, b, c}
-//   WIDE: a = level, b = rows per participating CTA, c = number of participating CTAs
-//   RUN : a = first block, b = end block, c = 0
+// CLUSTER: consecutive levels, each split in contiguous chunks over the CTAs of cluster 0.
+// int4 layout: {type | flags, a, b, c}
+//   WIDE   : a = level, b = rows per participating CTA, c = number of participating CTAs
+//   RUN    : a = first block, b = end block, c = 0
+//   CLUSTER: a = first level, b = end level, c = CTAs of the cluster
 // A run block: int4 {first level, end level, narrow (all levels fit one warp), 0}
 
 struct Schedule {
     int nrhs = -1, block = 0, run_width = 0, lpr = 0, grid = 0, ring_rows = 0;
+    int csize = 1;          // CTAs per cluster of the launch (1: no cluster segments, plain launch)
+    int cluster = 0;        // the system's cluster setting the schedule was built with
+    int64_t cluster_rows = 0;  // widest level run as a CLUSTER level
+    int64_t cluster_levels = 0;  // levels executed in CLUSTER segments
     int stage_rows = 0, stage_entries = 0;
     int pre = 0;       // a b-part kernel runs before the solve (rewritten rows in staged blocks)
     int pre_grid = 0;  // its CTAs
@@ -59,6 +78,7 @@ struct SolveArgs {
     int64_t timeout_ns;
     int ring_rows;  // power of two
     int lpr;        // lanes per row (power of two <= 32)
+    int csize;      // CTAs per cluster (1: launched without clusters)
     int stage_rows, stage_entries;
     int pre;        // xp holds the b-parts of the staged blocks' rows (k_bparts ran first)
 };
@@ -78,6 +98,8 @@ struct sptrsv_system {
     double avg = 0.0;
     // solve state
     int block = 512, run_width = 0, lpr = 0;  // 0: automatic
+    int cluster = 0;          // CTAs of the cluster that runs mid-width levels: 0 automatic, 1 none, 2..16
+    int64_t cluster_rows = 0; // widest level run on the cluster (0: automatic)
     sp::Schedule sched;
     std::vector<int32_t> h_cptr;  // host copy of cptr, for cutting run blocks
     sp::DevBuf<int> flags, status;
