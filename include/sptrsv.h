@@ -124,9 +124,11 @@ enum {
     SPTRSV_STRATEGY_CHOSEN = 4,  /* depth per target given by the caller */
     SPTRSV_STRATEGY_MANUAL = 5,  /* fixed distance k over thin levels only: the manual approach of the earlier work
                                     ("every 9 levels into the 10th", Sections III and IV) */
-    SPTRSV_STRATEGY_ROWCAP = 6   /* the Section III walk over thin levels with a row count in place of avgLevelCost:
+    SPTRSV_STRATEGY_ROWCAP = 6,  /* the Section III walk over thin levels with a row count in place of avgLevelCost:
                                     a target takes rows while it holds at most k of them (k <= 0: 32, one warp's
                                     lanes -- the width of a level in the fast thin-level executor) */
+    SPTRSV_STRATEGY_CHOSEN_THIN = 7 /* depth per target given by the caller, over thin levels only (cost below
+                                       avgLevelCost, Section III): the plan family of the learned strategy */
 };
 
 typedef struct {
@@ -137,8 +139,9 @@ typedef struct {
     double avg_override;           /* > 0: use this avgLevelCost instead of the computed one */
     double growth_guard;           /* > 0: fail with SPTRSV_ERR_NUMERIC if a rewritten coefficient exceeds it in magnitude */
     const sptrsv_picker* picker;   /* LEARNED */
-    const int32_t* depth_of_target_host; /* CHOSEN: depth for each level (m entries) when it is a target */
-    const int32_t* depths_host;    /* LEARNED: candidate depths (excluding 0); NULL = {1,2,4,8,16,32} */
+    const int32_t* depth_of_target_host; /* CHOSEN, CHOSEN_THIN: depth for each level (m entries) when it is a target */
+    const int32_t* depths_host;    /* LEARNED: candidates, a depth g >= 1 or a row budget -r (the largest depth whose
+                                      window holds at most r rows); NULL = {1,2,4,8,16,32,-16,-32,-64} */
     int32_t n_depths;              /* entries of depths_host */
     const int64_t* injected_cost_dev; /* test hook (NULL normally): per-row cost on the target used by
                                          the planner instead of 2 * |dependencies after substitution| */
@@ -188,6 +191,9 @@ typedef struct {
     int32_t cluster_setting; /* the system's cluster knob (0 automatic, 1 off, 2..16 CTAs) */
     int64_t cluster_levels; /* levels executed in CLUSTER segments */
     int64_t cluster_rows;  /* the system's widest-cluster-level knob (0 automatic) */
+    int64_t tiled_levels;  /* WIDE levels whose coefficients stream through shared-memory tiles */
+    int32_t tiles_setting; /* the system's tile knob (0 automatic, 1 never) */
+    int32_t reserved0;
 } sptrsv_system_info;
 
 sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);
@@ -271,11 +277,13 @@ sptrsv_status sptrsv_debug_set_wait(sptrsv_system* s, int64_t withhold_segment, 
  * kernel at all, one launch of a row-per-thread kernel per level), lanes per row. */
 sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_width, int32_t lanes_per_row);
 
-/* Cluster knobs of one system: levels wider than a single-CTA run and at most cluster_rows rows
- * (0: automatic, 16384) run as CLUSTER segments on the `cluster` CTAs of one thread-block cluster
- * (2..16; 0: automatic, 16; 1: no clusters), one cluster barrier per level instead of a
- * device-wide handoff.  Negative values keep the current setting.  No stream work. */
-sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows);
+/* Level-executor knobs of one system.  Levels wider than a single-CTA run and at most cluster_rows
+ * rows (0: automatic, 16384) run as CLUSTER segments on the `cluster` CTAs of one thread-block
+ * cluster (2..16; 0: automatic, 16; 1: no clusters), one cluster barrier per level instead of a
+ * device-wide handoff.  tiles 0 (automatic): without clusters, WIDE levels of one right-hand side
+ * stream their coefficients through shared memory in tiles (bulk copies, double-buffered) when
+ * they fit; tiles 1: never.  Negative values keep the current setting.  No stream work. */
+sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows, int32_t tiles);
 
 /* Autotuner: times candidate solves (b = 0) over lanes per row and the widest level
  * executed inside a single-CTA run, keeps the fastest for nrhs right-hand sides and
@@ -354,8 +362,10 @@ sptrsv_status sptrsv_picker_set_norm(sptrsv_picker* pk, const float* mean_host, 
 sptrsv_status sptrsv_picker_save(const sptrsv_picker* pk, const char* path);
 sptrsv_status sptrsv_picker_load(sptrsv_picker* pk, const char* path);
 
-/* Features of every candidate (target level t, depth g) for t in [0, m) and g in depths:
- * feat_dev[(t * n_depths + d) * 12 + f] (float32).  Stream-ordered. */
+/* Features of every candidate (target level t, candidate d) for t in [0, m):
+ * feat_dev[(t * n_depths + d) * 12 + f] (float32).  A candidate is a depth g >= 1 (the window
+ * t..t+g) or a row budget -r, which resolves per target to the largest depth whose window holds
+ * at most r rows (0 when level t alone holds more); 0 is rejected.  Stream-ordered. */
 sptrsv_status sptrsv_picker_features(const sptrsv_csr* L, const sptrsv_levels* lv, const int32_t* depths_host,
                                      int32_t n_depths, float* feat_dev, sptrsv_stream_t stream);
 

@@ -22,6 +22,11 @@ dependencies after one substitution).
   f10 cost(W) / avgLevelCost
   f11 fraction of levels of W with cost < avgLevelCost (thin levels)
 Computed in float64 and returned as float32.
+
+A candidate is a depth g >= 1, or a row budget given as a negative entry -r: then g is the
+largest depth whose window t..t+g holds at most r rows (0 when level t alone holds more), and
+the candidate's features are those of that window (a target that takes the following levels
+while it holds at most r rows, the row-capped strategy at the granularity of whole levels).
 """
 from __future__ import annotations
 
@@ -52,6 +57,20 @@ def level_aggregates(rowptr, colidx):
     return {"level": lev, "m": m, "rows": rows, "nnz": nnz, "cost": cost, "maxdeg": maxdeg, "twohop": twohop}
 
 
+def candidate_depth(rows, t, c) -> int:
+    """Depth of candidate c at target t: c itself when c >= 1; for c = -r the largest g with
+    rows(t) + ... + rows(t + g) <= r (t + g < m), found by adding levels one at a time."""
+    if c >= 1:
+        return int(c)
+    r, g, held = -int(c), 0, int(rows[t])
+    if held > r:
+        return 0
+    while t + g + 1 < len(rows) and held + int(rows[t + g + 1]) <= r:
+        g += 1
+        held += int(rows[t + g])
+    return g
+
+
 def features(rowptr, colidx, depths) -> np.ndarray:
     """Array (m * len(depths), 12), row t * len(depths) + d for candidate (t, depths[d])."""
     a = level_aggregates(rowptr, colidx)
@@ -60,7 +79,8 @@ def features(rowptr, colidx, depths) -> np.ndarray:
     avg = cost.sum() / m
     out = np.zeros((m * len(depths), 12), dtype=np.float64)
     for t in range(m):
-        for d, g in enumerate(depths):
+        for d, c in enumerate(depths):
+            g = candidate_depth(rows, t, c)
             te = min(t + g, m - 1)
             W = slice(t, te + 1)
             S = slice(t + 1, te + 1)

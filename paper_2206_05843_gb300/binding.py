@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsptrsv.so")
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC", 6: "UNSUPPORTED"}
 F64, F32 = 0, 1
-NONE, NAIVE, DEPTH_K, LEARNED, CHOSEN, MANUAL, ROWCAP = 0, 1, 2, 3, 4, 5, 6
+NONE, NAIVE, DEPTH_K, LEARNED, CHOSEN, MANUAL, ROWCAP, CHOSEN_THIN = 0, 1, 2, 3, 4, 5, 6, 7
 PICKER_FEATURES, PICKER_HIDDEN = 12, 64
 PICKER_PARAMS = 12 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 
@@ -70,7 +70,8 @@ class SystemInfo(C.Structure):
                 ("run_width", C.c_int32), ("lanes_per_row", C.c_int32), ("strategy_used", C.c_int32),
                 ("launches", C.c_int32), ("ctas", C.c_int32), ("candidate_us", C.c_double * 4),
                 ("cluster", C.c_int32), ("cluster_setting", C.c_int32), ("cluster_levels", C.c_int64),
-                ("cluster_rows", C.c_int64)]
+                ("cluster_rows", C.c_int64), ("tiled_levels", C.c_int64), ("tiles_setting", C.c_int32),
+                ("reserved0", C.c_int32)]
 
 
 class BatchInfo(C.Structure):
@@ -109,7 +110,7 @@ def load():
             "sptrsv_debug_set_wait": [vp, i64, i64],
             "sptrsv_debug_run_blocks": [vp, i64, vp, i32, i32, i32, vp, i64, vp, vp],
             "sptrsv_system_tune": [vp, i32, i32, i32],
-            "sptrsv_system_tune_cluster": [vp, i32, i64],
+            "sptrsv_system_tune_cluster": [vp, i32, i64, i32],
             "sptrsv_system_autotune": [vp, i32, vp, vp],
             "sptrsv_upper_to_lower": [vp, vp, vp, vp, vp],
             "sptrsv_system_reverse_rows": [vp, vp],
@@ -313,9 +314,10 @@ class System:
     def tune(self, block=0, run_width=0, lanes_per_row=0):
         check(load().sptrsv_system_tune(self.h, block, run_width, lanes_per_row))
 
-    def tune_cluster(self, cluster=-1, cluster_rows=-1):
-        """CTAs per cluster for mid-width levels (0 automatic, 1 none) and the widest such level."""
-        check(load().sptrsv_system_tune_cluster(self.h, cluster, cluster_rows))
+    def tune_cluster(self, cluster=-1, cluster_rows=-1, tiles=-1):
+        """CTAs per cluster for mid-width levels (0 automatic, 1 none), the widest such level, and
+        whether wide levels may stream through shared-memory tiles (0 automatic, 1 never)."""
+        check(load().sptrsv_system_tune_cluster(self.h, cluster, cluster_rows, tiles))
 
     def autotune(self, nrhs=1) -> float:
         """Times candidate schedules and keeps the fastest; returns its time in us."""
@@ -495,7 +497,9 @@ class Picker:
             pass
 
 
-DEFAULT_DEPTHS = (1, 2, 4, 8, 16, 32)
+# candidates of the learned strategy: fixed depths, and row budgets as negative entries (a target
+# takes the following levels while it holds at most r rows)
+DEFAULT_DEPTHS = (1, 2, 4, 8, 16, 32, -16, -32, -64)
 
 
 def features(matrix: Matrix, levels: Levels, depths=DEFAULT_DEPTHS):

@@ -120,6 +120,35 @@ __device__ __forceinline__ uint64_t globaltimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// mbarrier and bulk-copy helpers (shared::cta addresses)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* m, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+// makes initialised mbarriers visible to the bulk-copy unit
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// one arrival that also expects `bytes` of bulk-copy transactions in the current phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) that completes
+// its bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(m))
+                 : "memory");
+}
+
 // Asks the TMA unit to bring [p, p + bytes) into L2 without waiting for it: the threads of
 // the CTA issue one bulk prefetch per 4 KB piece.  Only the 16-byte aligned interior of the
 // range is prefetched (the bulk copy's alignment rule), so nothing outside it is touched.
@@ -132,6 +161,14 @@ __device__ __forceinline__ void l2_prefetch(const void* p, int64_t bytes) {
         const uint32_t n = (uint32_t)(e - q < PIECE ? e - q : PIECE);
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
     }
+}
+// waits for the mbarrier phase of the given parity; false when timeout_ns passes first
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity, int64_t timeout_ns) {
+    if (mbar_try_wait(m, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(m, parity))
+        if (globaltimer() - t0 > (uint64_t)timeout_ns) return false;
+    return true;
 }
 #endif
 

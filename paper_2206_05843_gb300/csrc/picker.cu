@@ -13,6 +13,9 @@
 #include <cstdio>
 #include <cstring>
 #include <random>
+#include <string>
+#include <thread>
+#include <vector>
 
 #include "system.cuh"
 
@@ -62,13 +65,30 @@ struct FeatArgs {
     int nd;
     double avg;
     float* out;
+    int32_t* gsel;  // depth each candidate resolves to (may be null)
 };
+
+// A candidate is a depth g >= 1 or a row budget -r: the largest depth whose window t..t+g holds at
+// most r rows (0 when level t alone holds more) -- a binary search on the level-row prefix sums
+__device__ int candidate_depth(const int64_t* prow, int64_t m, int64_t t, int c) {
+    if (c >= 1) return c;
+    const int64_t r = -(int64_t)c;
+    if (prow[t + 1] - prow[t] > r) return 0;
+    int64_t lo = t, hi = m - 1;  // largest e in [t, m-1] with prow[e+1] - prow[t] <= r
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (prow[mid + 1] - prow[t] <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return (int)(lo - t);
+}
 
 __global__ void k_features(FeatArgs a) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= a.m * a.nd) return;
     const int64_t t = idx / a.nd;
-    const int g = a.depths[idx % a.nd];
+    const int g = candidate_depth(a.prow, a.m, t, a.depths[idx % a.nd]);
+    if (a.gsel) a.gsel[idx] = g;
     const int64_t te = min(t + (int64_t)g, a.m - 1);
     auto sum = [&](const int64_t* p, int64_t lo, int64_t hi) { return hi >= lo ? p[hi + 1] - p[lo] : (int64_t)0; };
     const double rW = (double)sum(a.prow, t, te), nW = (double)sum(a.pnnz, t, te);
@@ -238,7 +258,8 @@ __global__ void k_to_bf16(const float* p, __nv_bfloat16* p16) {
 }
 
 // depth per level: the candidate with the lowest predicted change, 0 if none is negative
-__global__ void k_choose_depths(int64_t m, const float* pred, const int32_t* depths, int nd, int32_t* dot) {
+// (gsel: the depth each candidate resolves to)
+__global__ void k_choose_depths(int64_t m, const float* pred, const int32_t* gsel, int nd, int32_t* dot) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m) return;
     int best = 0;
@@ -247,13 +268,14 @@ __global__ void k_choose_depths(int64_t m, const float* pred, const int32_t* dep
         const float v = pred[t * nd + d];
         if (v < bv) {
             bv = v;
-            best = depths[d];
+            best = gsel[t * nd + d];
         }
     }
     dot[t] = best;
 }
 
-constexpr int DEFAULT_DEPTHS[] = {1, 2, 4, 8, 16, 32};
+// fixed depths and row budgets (negative: a target takes levels while it holds at most r rows)
+constexpr int DEFAULT_DEPTHS[] = {1, 2, 4, 8, 16, 32, -16, -32, -64};
 
 }  // namespace
 }  // namespace sp
@@ -321,7 +343,7 @@ sptrsv_status grad_impl(const sptrsv_picker* pk, const float* X, const float* t,
 
 // per-level aggregates, prefix sums and the feature kernel
 sptrsv_status features_impl(const sptrsv_csr* L, const Levels& lv, const int32_t* depths_host, int nd, float* out,
-                            cudaStream_t st) {
+                            int32_t* gsel, cudaStream_t st) {
     const int64_t n = L->n, m = lv.m;
     if (m == 0) return SPTRSV_OK;
     Scratch maxdeg, two, thin, pre, dep;
@@ -356,6 +378,7 @@ sptrsv_status features_impl(const sptrsv_csr* L, const Levels& lv, const int32_t
     a.nd = nd;
     a.avg = lv.avg;
     a.out = out;
+    a.gsel = gsel;
     k_features<<<nblk(m * nd, 256), 256, 0, st>>>(a);
     SP_CUDA(cudaGetLastError());
     SP_CUDA(cudaStreamSynchronize(st));  // the scratch above is released after the kernel
@@ -370,55 +393,78 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
     const int32_t* depths = sg->depths_host && sg->n_depths > 0 ? sg->depths_host : DEFAULT_DEPTHS;
     const int nd = sg->depths_host && sg->n_depths > 0 ? sg->n_depths : (int)(sizeof(DEFAULT_DEPTHS) / sizeof(int));
     const int64_t m = lv.m;
-    Scratch feat, pred, dot, dep;
+    Scratch feat, pred, dot, gsel;
     SP_TRY(feat.alloc(std::max<int64_t>(1, m * nd) * NF * 4, st));
     SP_TRY(pred.alloc(std::max<int64_t>(1, m * nd) * 4, st));
     SP_TRY(dot.alloc(std::max<int64_t>(1, m) * 4, st));
-    SP_TRY(dep.alloc(nd * 4, st));
-    SP_TRY(features_impl(L, lv, depths, nd, feat.as<float>(), st));
+    SP_TRY(gsel.alloc(std::max<int64_t>(1, m * nd) * 4, st));
+    SP_TRY(features_impl(L, lv, depths, nd, feat.as<float>(), gsel.as<int32_t>(), st));
     SP_TRY(forward(sg->picker, feat.as<float>(), m * nd, pred.as<float>(), nullptr, 1, st));
-    SP_CUDA(cudaMemcpyAsync(dep.p, depths, nd * 4, cudaMemcpyHostToDevice, st));
-    if (m > 0) k_choose_depths<<<nblk(m, 256), 256, 0, st>>>(m, pred.as<float>(), dep.as<int32_t>(), nd, dot.as<int32_t>());
+    if (m > 0) k_choose_depths<<<nblk(m, 256), 256, 0, st>>>(m, pred.as<float>(), gsel.as<int32_t>(), nd, dot.as<int32_t>());
     SP_CUDA(cudaGetLastError());
-    sptrsv_system* model = nullptr;
-    SP_TRY(rewrite_system(L, lv, 5 /* depth per thin target */, 0, dot.as<int32_t>(), sg->avg_override, sg->nnz_growth_cap,
-                          sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &model, st));
-    model->strategy_used = SPTRSV_STRATEGY_CHOSEN;
     if (sg->learned_mode == 1) {
+        sptrsv_system* model = nullptr;
+        SP_TRY(rewrite_system(L, lv, 5 /* depth per thin target */, 0, dot.as<int32_t>(), sg->avg_override,
+                              sg->nnz_growth_cap, sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &model, st));
+        model->strategy_used = SPTRSV_STRATEGY_CHOSEN;
         *out = model;
         return SPTRSV_OK;
     }
-    // the paper's naive strategy is the fallback; the measured solve time decides
-    sptrsv_system* naive = nullptr;
-    sptrsv_status rc = rewrite_system(L, lv, 1 /* naive */, 0, nullptr, sg->avg_override, sg->nnz_growth_cap,
-                                      sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &naive, st);
-    if (rc != SPTRSV_OK) {
-        sptrsv_system_destroy(model);
-        return rc;
-    }
-    naive->strategy_used = SPTRSV_STRATEGY_NAIVE;
-    // the plan shaped for the fast executor (targets of at most one warp's rows)
-    sptrsv_system* rowcap = nullptr;
-    rc = rewrite_system(L, lv, 6 /* rowcap */, ROWCAP_DEFAULT_ROWS, nullptr, sg->avg_override, sg->nnz_growth_cap,
-                        sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &rowcap, st);
-    if (rc != SPTRSV_OK) {
-        sptrsv_system_destroy(model);
-        sptrsv_system_destroy(naive);
-        return rc;
-    }
-    rowcap->strategy_used = SPTRSV_STRATEGY_ROWCAP;
-    // and not rewriting at all: the plain level-set system
-    sptrsv_system* plain = nullptr;
-    rc = sptrsv_system_plain(L, lvh, &plain, st);
-    if (rc != SPTRSV_OK) {
-        sptrsv_system_destroy(model);
-        sptrsv_system_destroy(naive);
-        sptrsv_system_destroy(rowcap);
-        return rc;
-    }
-    plain->strategy_used = SPTRSV_STRATEGY_NONE;
+    // Candidates: the model's plan, the paper's naive strategy, the plan shaped for the fast executor
+    // (targets of at most one warp's rows) and no rewrite; the measured solve time decides.  The three
+    // plans are independent (each planner walk is one warp for the length of the level sequence), so
+    // they are built at the same time, each by a host thread on a stream of its own.
     constexpr int NC = 4;
-    sptrsv_system* cand[NC] = {model, naive, rowcap, plain};
+    sptrsv_system* cand[NC] = {nullptr, nullptr, nullptr, nullptr};
+    sptrsv_status crc[NC] = {SPTRSV_OK, SPTRSV_OK, SPTRSV_OK, SPTRSV_OK};
+    std::string cerr[NC];
+    int dev = 0;
+    SP_CUDA(cudaGetDevice(&dev));
+    cudaEvent_t ready;
+    SP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    SP_CUDA(cudaEventRecord(ready, st));  // the depths per target are on `st`
+    const int kinds[3] = {5 /* depth per thin target */, 1 /* naive */, 6 /* rowcap */};
+    const int used[3] = {SPTRSV_STRATEGY_CHOSEN, SPTRSV_STRATEGY_NAIVE, SPTRSV_STRATEGY_ROWCAP};
+    std::vector<std::thread> workers;
+    for (int i = 0; i < 3; ++i) {
+        workers.emplace_back([&, i]() {
+            cudaStream_t ws = nullptr;
+            sptrsv_status rc = SPTRSV_OK;
+            if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
+                set_error("learned strategy: stream setup failed");
+                rc = SPTRSV_ERR_CUDA;
+            } else {
+                rc = rewrite_system(L, lv, kinds[i], kinds[i] == 6 ? ROWCAP_DEFAULT_ROWS : 0,
+                                    kinds[i] == 5 ? dot.as<int32_t>() : nullptr, sg->avg_override, sg->nnz_growth_cap,
+                                    sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &cand[i], ws);
+                if (rc == SPTRSV_OK && cudaStreamSynchronize(ws) != cudaSuccess) {
+                    set_error("learned strategy: candidate plan failed");
+                    rc = SPTRSV_ERR_CUDA;
+                }
+            }
+            if (ws) cudaStreamDestroy(ws);
+            crc[i] = rc;
+            if (rc != SPTRSV_OK) cerr[i] = get_error();
+            else cand[i]->strategy_used = used[i];
+        });
+    }
+    crc[3] = sptrsv_system_plain(L, lvh, &cand[3], st);
+    if (crc[3] == SPTRSV_OK) cand[3]->strategy_used = SPTRSV_STRATEGY_NONE;
+    else cerr[3] = get_error();
+    for (auto& w : workers) w.join();
+    cudaEventDestroy(ready);
+    sptrsv_status rc = SPTRSV_OK;
+    for (int i = 0; i < NC; ++i)
+        if (crc[i] != SPTRSV_OK && rc == SPTRSV_OK) {
+            rc = crc[i];
+            set_error("%s", cerr[i].c_str());
+        }
+    if (rc != SPTRSV_OK) {
+        for (sptrsv_system* c : cand)
+            if (c) sptrsv_system_destroy(c);
+        return rc;
+    }
     double t[NC] = {0, 0, 0, 0};
     for (int i = 0; i < NC && rc == SPTRSV_OK; ++i) rc = time_solve_us(cand[i], 5, &t[i], st);
     if (rc != SPTRSV_OK) {
@@ -556,7 +602,9 @@ sptrsv_status sptrsv_picker_load(sptrsv_picker* pk, const char* path) {
 sptrsv_status sptrsv_picker_features(const sptrsv_csr* L, const sptrsv_levels* lv, const int32_t* depths, int32_t nd,
                                      float* feat, sptrsv_stream_t stream) {
     if (!L || !lv || !depths || nd < 1 || !feat) { set_error("picker_features: bad argument"); return SPTRSV_ERR_INVALID; }
-    return features_impl(L, lv->lv, depths, nd, feat, (cudaStream_t)stream);
+    for (int d = 0; d < nd; ++d)
+        if (depths[d] == 0) { set_error("picker_features: a candidate is a depth >= 1 or a row budget < 0"); return SPTRSV_ERR_INVALID; }
+    return features_impl(L, lv->lv, depths, nd, feat, nullptr, (cudaStream_t)stream);
 }
 
 sptrsv_status sptrsv_picker_infer(const sptrsv_picker* pk, const float* feat, int64_t count, float* out, int32_t bf16,

@@ -251,12 +251,22 @@ __global__ void k_init_walk(int64_t n, const int32_t* rowptr, const int32_t* lev
     row_cost[i] = 2 * ((int64_t)rowptr[i + 1] - rowptr[i]) - 1;
 }
 
-// fixed depths without a cap: every level maps to its target independently of the rows
-__global__ void k_level_targets(int64_t m, int kind, int k, const int32_t* dot, int32_t* ltarget) {
+// fixed depths without a cap: every level maps to its target independently of the rows (over all
+// levels for DEPTH and CHOSEN; over thin levels, cost below avgLevelCost, for MANUAL and CHOSEN_THIN,
+// where a level that is not thin keeps its rows and ends the group)
+__global__ void k_level_targets(int64_t m, int kind, int k, const int32_t* dot, const int64_t* lcost, double avg,
+                                int32_t* ltarget) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const bool thin_only = kind == WALK_MANUAL || kind == WALK_CHOSEN_THIN;
+    const bool by_dot = kind == WALK_CHOSEN || kind == WALK_CHOSEN_THIN;
     int64_t t = -1;
     for (int64_t s = 0; s < m; ++s) {
-        if (t < 0 || (kind == WALK_DEPTH && s - t > k) || (kind == WALK_CHOSEN && s - t > dot[t])) t = s;
+        if (thin_only && !((double)lcost[s] < avg)) {
+            t = -1;
+            ltarget[s] = (int32_t)s;
+            continue;
+        }
+        if (t < 0 || (!by_dot && s - t > k) || (by_dot && s - t > dot[t])) t = s;
         ltarget[s] = (int32_t)t;
     }
 }
@@ -488,12 +498,12 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
                            double avg, double cap, const int64_t* inj, int alpha, int64_t beta, int32_t* target,
                            PlanOut& po, cudaStream_t st) {
     const int64_t n = L->n, m = lv.m;
-    const bool walk = kind == WALK_NAIVE || kind == WALK_MANUAL || kind == WALK_CHOSEN_THIN || kind == WALK_ROWCAP ||
-                      cap > 0 || inj || alpha > 0 || beta > 0;
+    // the row walk is needed where the rows decide (cost or row budget, the nnz cap, the per-row rules)
+    const bool walk = kind == WALK_NAIVE || kind == WALK_ROWCAP || cap > 0 || inj || alpha > 0 || beta > 0;
     if (!walk) {
         Scratch lt;
         SP_TRY(lt.alloc(std::max<int64_t>(1, m) * sizeof(int32_t), st));
-        k_level_targets<<<1, 1, 0, st>>>(m, kind, k, dot_dev, lt.as<int32_t>());
+        k_level_targets<<<1, 1, 0, st>>>(m, kind, k, dot_dev, lv.lcost.p, avg, lt.as<int32_t>());
         k_map_targets<<<nblk(n, 256), 256, 0, st>>>(n, lv.level.p, lt.as<int32_t>(), target);
         SP_CUDA(cudaGetLastError());
         return SPTRSV_OK;
@@ -759,7 +769,7 @@ extern "C" sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels
     }
     Scratch dot;
     const int32_t* dot_dev = nullptr;
-    if (kind == SPTRSV_STRATEGY_CHOSEN) {
+    if (kind == SPTRSV_STRATEGY_CHOSEN || kind == SPTRSV_STRATEGY_CHOSEN_THIN) {
         if (!sg->depth_of_target_host) { set_error("rewrite: CHOSEN needs depth_of_target"); return SPTRSV_ERR_INVALID; }
         SP_TRY(dot.alloc(std::max<int64_t>(1, lv.m) * 4, st));
         SP_CUDA(cudaMemcpyAsync(dot.p, sg->depth_of_target_host, lv.m * 4, cudaMemcpyHostToDevice, st));
@@ -767,7 +777,7 @@ extern "C" sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels
     }
     int wk = kind == SPTRSV_STRATEGY_NAIVE ? WALK_NAIVE : kind == SPTRSV_STRATEGY_DEPTH_K ? WALK_DEPTH
            : kind == SPTRSV_STRATEGY_CHOSEN ? WALK_CHOSEN : kind == SPTRSV_STRATEGY_MANUAL ? WALK_MANUAL
-           : kind == SPTRSV_STRATEGY_ROWCAP ? WALK_ROWCAP : 0;
+           : kind == SPTRSV_STRATEGY_ROWCAP ? WALK_ROWCAP : kind == SPTRSV_STRATEGY_CHOSEN_THIN ? WALK_CHOSEN_THIN : 0;
     if (!wk) { set_error("rewrite: unknown strategy %d", kind); return SPTRSV_ERR_INVALID; }
     const int k = kind == SPTRSV_STRATEGY_ROWCAP && sg->k <= 0 ? ROWCAP_DEFAULT_ROWS : sg->k;
     sptrsv_status rc = rewrite_system(L, lv, wk, k, dot_dev, sg->avg_override, sg->nnz_growth_cap,

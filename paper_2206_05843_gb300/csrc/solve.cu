@@ -53,6 +53,7 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     a.stage_entries = sc.stage_entries;
     a.pre = sc.pre;
     a.csize = sc.csize;
+    a.tile_ecap = sc.tile_ecap;
 
     SP_CUDA(cudaMemsetAsync(s->flags.p, 0xff, (size_t)sc.grid * sizeof(int), st));
     SP_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
@@ -69,6 +70,7 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     }
     if (a.nseg == 0) return SPTRSV_OK;
     if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
+    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize, sc.tile_ecap));  // systems may differ in their shared memory
     SP_CUDA(launch_k_solve<T>(a, sc.grid, sc.block, sc.smem, sc.csize, st));
     return SPTRSV_OK;
 }
@@ -76,12 +78,12 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
 // CTAs of the persistent kernel that can be co-resident with the given block, shared memory and
 // cluster size (cluster size 1: no clusters); 0 when the configuration does not fit.
 template <typename T>
-sptrsv_status solve_capacity(int block, size_t smem, int csize, int64_t* ctas) {
+sptrsv_status solve_capacity(int block, size_t smem, int csize, int tiled, int64_t* ctas) {
     *ctas = 0;
-    SP_CUDA(k_solve_attrs<T>(smem, csize));
+    SP_CUDA(k_solve_attrs<T>(smem, csize, tiled));
     if (csize <= 1) {
         int occ = 0;
-        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve<T, false>, block, smem));
+        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_fn<T>(k_mode(1, tiled)), block, smem));
         *ctas = (int64_t)device_sm_count() * occ;
         return SPTRSV_OK;
     }
@@ -97,7 +99,7 @@ sptrsv_status solve_capacity(int block, size_t smem, int csize, int64_t* ctas) {
     q.attrs = at;
     q.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_solve<T, true>, &q) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_solve_fn<T>(KM_CLUSTER), &q) != cudaSuccess) {
         cudaGetLastError();  // a cluster size the device cannot place: no clusters
         ncl = 0;
     }
@@ -230,7 +232,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
         return SPTRSV_ERR_INVALID;
     }
     if (sc.nrhs == nrhs && sc.lpr == lpr && sc.block == block && sc.run_width == s->run_width &&
-        sc.cluster == s->cluster && sc.cluster_rows == s->cluster_rows && sc.segs.p)
+        sc.cluster == s->cluster && sc.cluster_rows == s->cluster_rows && sc.tiles == s->tiles && sc.segs.p)
         return SPTRSV_OK;
     const int ngroups = block / lpr;
     // shared memory: two staging buffers + an x ring of at least twice the staged rows
@@ -249,6 +251,8 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     sc.h_segs.clear();
     sc.h_blocks.clear();
     sc.run_levels = 0;
+    sc.tile_ecap = 0;
+    sc.tiled_levels = 0;
     int64_t max_parts = 1;
     int sms = device_sm_count();
     // occupancy decides the number of CTAs that WIDE levels can be split over
@@ -256,13 +260,23 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     int64_t gplain = 0, gcl = 0;
     int csize = s->cluster == 1 ? 1 : (s->cluster > 1 ? std::min(16, s->cluster) : CLUSTER_DEFAULT);
     const int64_t cl_rows = s->cluster_rows > 0 ? s->cluster_rows : CLUSTER_ROWS_DEFAULT;
-    if (s->dtype == SPTRSV_F64) {
-        SP_TRY(solve_capacity<double>(block, smem, 1, &gplain));
-        if (csize > 1) SP_TRY(solve_capacity<double>(block, smem, csize, &gcl));
-    } else {
-        SP_TRY(solve_capacity<float>(block, smem, 1, &gplain));
-        if (csize > 1) SP_TRY(solve_capacity<float>(block, smem, csize, &gcl));
+    auto capacity = [&](size_t sm, int cs, int tiled, int64_t* out) -> sptrsv_status {
+        return s->dtype == SPTRSV_F64 ? solve_capacity<double>(block, sm, cs, tiled, out)
+                                      : solve_capacity<float>(block, sm, cs, tiled, out);
+    };
+    // wide levels of one right-hand side may stream their coefficients through shared memory
+    // (two tile buffers; the kernel variant with tiled WIDE levels, so schedules with CLUSTER
+    // segments do not tile), when that does not lower the number of co-resident CTAs
+    bool tiles_ok = nrhs == 1 && block == TILE_ROWS && s->tiles != 1;
+    const size_t smem_tiles = std::max(smem, (size_t)TILE_SMEM_MAX);
+    if (tiles_ok) {
+        int64_t g_run = 0, g_tiles = 0;
+        SP_TRY(capacity(smem, 1, 0, &g_run));
+        SP_TRY(capacity(smem_tiles, 1, 1, &g_tiles));
+        tiles_ok = g_tiles == g_run;
     }
+    SP_TRY(capacity(tiles_ok ? smem_tiles : smem, 1, tiles_ok ? 1 : 0, &gplain));
+    if (csize > 1) SP_TRY(capacity(smem, csize, 0, &gcl));
     if (gplain < 1) {
         set_error("solve kernel does not fit an SM with block %d and %zu bytes of shared memory", block, smem);
         return SPTRSV_ERR_UNSUPPORTED;
@@ -294,6 +308,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     } else {
         csize = 1;
     }
+    if (csize > 1) tiles_ok = false;
     const int64_t gmax = csize > 1 ? gcl : gplain;
     sc.cluster_levels = 0;
     int64_t l = 0;
@@ -336,7 +351,29 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
             int64_t parts = (w + per - 1) / per;
             if (per >= INT32_MAX) { set_error("level too wide"); return SPTRSV_ERR_UNSUPPORTED; }
             max_parts = std::max(max_parts, parts);
-            sc.h_segs.push_back(make_int4(SEG_WIDE | (wl == lpr ? 0 : wl << SEG_LPR_SHIFT), (int)l, (int)per, (int)parts));
+            int flags = SEG_WIDE | (wl == lpr ? 0 : wl << SEG_LPR_SHIFT);
+            if (tiles_ok && wl == 1) {
+                // the largest tile (512, 256 or 128 rows) whose coefficients fit a buffer in every tile
+                for (int sh = 0; sh < 3; ++sh) {
+                    const int64_t tr = TILE_ROWS >> sh;
+                    if ((per + tr - 1) / tr > TILE_MAX) break;
+                    int64_t emax = 0;
+                    for (int64_t c = 0; c < parts; ++c) {  // tiles of every CTA's share
+                        const int64_t s0 = lp[l] + c * per, s1 = std::min<int64_t>(lp[l + 1], s0 + per);
+                        for (int64_t r0 = s0; r0 < s1; r0 += tr) {
+                            const int64_t r1 = std::min(r0 + tr, s1);
+                            emax = std::max<int64_t>(emax, (int64_t)hcptr[r1] - hcptr[r0]);
+                        }
+                    }
+                    if (2 * tile_buf_bytes(emax, vb) <= (size_t)TILE_SMEM_MAX) {
+                        flags |= SEG_TILED | (sh << SEG_TILE_SHIFT);
+                        sc.tile_ecap = (int)std::max<int64_t>(sc.tile_ecap, std::max<int64_t>(emax, 16));
+                        sc.tiled_levels += 1;
+                        break;
+                    }
+                }
+            }
+            sc.h_segs.push_back(make_int4(flags, (int)l, (int)per, (int)parts));
             ++l;
         }
     }
@@ -369,6 +406,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     sc.csize = csize;
     sc.cluster = s->cluster;
     sc.cluster_rows = s->cluster_rows;
+    sc.tiles = s->tiles;
     sc.nrhs = nrhs;
     sc.lpr = lpr;
     sc.block = block;
@@ -376,7 +414,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     sc.ring_rows = ring_rows;
     sc.stage_rows = stage_rows;
     sc.stage_entries = stage_entries;
-    sc.smem = smem;
+    sc.smem = sc.tile_ecap > 0 ? std::max(smem, 2 * tile_buf_bytes(sc.tile_ecap, vb)) : smem;
     SP_TRY(s->flags.ensure((size_t)std::max(1, sc.grid)));
     SP_TRY(s->status.ensure(1));
     return SPTRSV_OK;
@@ -412,6 +450,7 @@ struct TuneVal {
     double us;
     int cluster = 0;
     int64_t cluster_rows = 0;
+    int tiles = 0;
 };
 std::mutex g_stune_mu;
 std::map<TuneKey, TuneVal> g_stune_cache;
@@ -437,6 +476,7 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
             s->lpr = f->second.lpr;
             s->cluster = f->second.cluster;
             s->cluster_rows = f->second.cluster_rows;
+            s->tiles = f->second.tiles;
             if (best_us) *best_us = f->second.us;
             return prepare_schedule(s, nrhs);
         }
@@ -461,7 +501,7 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
     SP_CUDA(cudaEventCreate(&e0));
     SP_CUDA(cudaEventCreate(&e1));
     TuneVal best{512, 0, 0, 1e300};
-    const int old_block = s->block, old_rw = s->run_width, old_lpr = s->lpr, old_cl = s->cluster;
+    const int old_block = s->block, old_rw = s->run_width, old_lpr = s->lpr, old_cl = s->cluster, old_tl = s->tiles;
     const int64_t old_clr = s->cluster_rows;
     sptrsv_status rc = SPTRSV_OK;
     // best of 3 timed solves of the current settings, in microseconds
@@ -481,23 +521,25 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         *us = bestms * 1e3;
         return SPTRSV_OK;
     };
-    // lanes per row x widest single-CTA level x the cluster that runs mid-width levels (none, 16
-    // or 8 CTAs); then the widest cluster level for the best of those
-    const int cls[][2] = {{1, 0}, {16, 16384}, {8, 16384}};
+    // lanes per row x widest single-CTA level x {no cluster with and without tiled wide levels,
+    // a cluster of 16 or 8 CTAs for mid-width levels}; then the widest cluster level for the best
+    const int cls[][3] = {{1, 0, 0}, {1, 0, 1}, {16, 16384, 1}, {8, 16384, 1}};
     for (int lpr : lprs) {
         for (int rw : widths) {
             if (rw == -2 && lpr != lprs[0]) continue;
             for (const auto& c : cls) {
-                if (rw == -2 && c[0] != 1) continue;  // one launch per level has no clusters
+                if (rw == -2 && (c[0] != 1 || c[2] != 1)) continue;  // one launch per level: no clusters, no tiles
+                if (nrhs > 1 && c[0] == 1 && c[2] == 0) continue;   // tiles are for one right-hand side
                 s->block = 512;
                 s->run_width = rw;
                 s->lpr = lpr;
                 s->cluster = c[0];
                 s->cluster_rows = c[1];
+                s->tiles = c[2];
                 double us = 0;
                 rc = time_current(&us);
                 if (rc != SPTRSV_OK) break;
-                if (us < best.us) best = TuneVal{512, rw, lpr, us, c[0], c[1]};
+                if (us < best.us) best = TuneVal{512, rw, lpr, us, c[0], c[1], c[2]};
             }
             if (rc != SPTRSV_OK) break;
         }
@@ -508,12 +550,13 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         s->run_width = best.run_width;
         s->lpr = best.lpr;
         s->cluster = best.cluster;
+        s->tiles = best.tiles;
         for (int64_t rows : {(int64_t)4096, (int64_t)65536}) {
             s->cluster_rows = rows;
             double us = 0;
             rc = time_current(&us);
             if (rc != SPTRSV_OK) break;
-            if (us < best.us) best = TuneVal{best.block, best.run_width, best.lpr, us, best.cluster, rows};
+            if (us < best.us) best = TuneVal{best.block, best.run_width, best.lpr, us, best.cluster, rows, best.tiles};
         }
     }
     cudaEventDestroy(e0);
@@ -524,6 +567,7 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         s->lpr = old_lpr;
         s->cluster = old_cl;
         s->cluster_rows = old_clr;
+        s->tiles = old_tl;
         s->sched.nrhs = -1;
         return rc;
     }
@@ -533,6 +577,7 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
     s->lpr = best.lpr;
     s->cluster = best.cluster;
     s->cluster_rows = best.cluster_rows;
+    s->tiles = best.tiles;
     s->sched.nrhs = -1;
     {
         std::lock_guard<std::mutex> lk(g_stune_mu);

@@ -302,6 +302,126 @@ __global__ void k_stamp(unsigned long long* stamps, int64_t l) {
 // the kernel
 // ---------------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------------
+// wide levels of one right-hand side with the coefficients streamed through shared memory
+// ---------------------------------------------------------------------------------
+
+// The CTA's share [my0, my1) of a level is cut into tiles of TR rows (one thread per row).  The
+// columns and values of a tile are one contiguous range of the stored arrays; thread 0 copies it
+// into one of two shared-memory buffers with two bulk copies on that buffer's mbarrier, two tiles
+// ahead of the compute (the first two before the handoff wait, since they do not depend on x).
+// A thread keeps its row's position data for the next tile in registers; x gathers read L2.
+// the two buffers' mbarriers, the first coefficient of every tile of the CTA's share, and the
+// buffers themselves (the dynamic shared memory, which RUN segments use for staging)
+__shared__ __align__(8) uint64_t g_tile_mbar[2];
+__shared__ int32_t g_tile_q[TILE_MAX + 1];
+extern __shared__ __align__(16) unsigned char g_dyn_smem[];
+
+struct TileCtx {
+    uint32_t k;  // tile copies this CTA has issued so far (buffer k & 1, phase k >> 1)
+};
+
+template <typename T>
+__device__ __forceinline__ void tile_issue(const SolveArgs<T>& a, int i, uint32_t slot) {
+    constexpr int VA = 16 / (int)sizeof(T);  // values per 16 bytes
+    const int q0 = g_tile_q[i], q1 = g_tile_q[i + 1];
+    const int qa = q0 & ~3, qv = q0 & ~(VA - 1);  // 16-byte starts of the two copies
+    const uint32_t cb = (uint32_t)align16((size_t)(q1 - qa) * 4);
+    const uint32_t vbytes = (uint32_t)align16((size_t)(q1 - qv) * sizeof(T));
+    unsigned char* base = g_dyn_smem + (size_t)slot * tile_buf_bytes(a.tile_ecap, (int)sizeof(T));
+    uint64_t* m = g_tile_mbar + slot;
+    mbar_arrive_expect_tx(m, cb + vbytes);
+    if (cb) bulk_g2s(base, a.ccol + qa, cb, m);
+    if (vbytes) bulk_g2s(base + align16((size_t)(a.tile_ecap + 4) * 4), a.cval + qv, vbytes, m);
+}
+
+// bounded wait for tile copies [i0, i1) that were issued and not yet consumed (after a failure)
+template <typename T>
+__device__ void tile_drain(const SolveArgs<T>& a, const TileCtx& c, int i0, int i1) {
+    for (int i = i0; i < i1; ++i) {
+        const uint32_t kk = c.k + (uint32_t)i;
+        mbar_wait_bounded(g_tile_mbar + (kk & 1), (kk >> 1) & 1, a.timeout_ns);
+    }
+}
+
+template <typename T, typename WaitFn>
+__device__ bool wide_rows_tiled(const SolveArgs<T>& a, int64_t my0, int64_t my1, int TR, TileCtx& c, WaitFn wait) {
+    constexpr int VA = 16 / (int)sizeof(T);
+    const int t = threadIdx.x;
+    const int nt = my1 > my0 ? (int)((my1 - my0 + TR - 1) / TR) : 0;  // the schedule keeps nt <= TILE_MAX
+    for (int i = t; i <= nt; i += blockDim.x) g_tile_q[i] = a.cptr[min(my1, my0 + (int64_t)i * TR)];
+    // the buffers may hold a single-CTA run's staging, written by the threads: order those writes
+    // before the bulk copies that overwrite them
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const int pre_issued = nt < 2 ? nt : 2;
+    if (t == 0)
+        for (int i = 0; i < pre_issued; ++i) tile_issue(a, i, (c.k + i) & 1);
+    // this thread's row of tile 0
+    int64_t p = my0 + t;
+    bool act = t < TR && p < my1;
+    int32_t row = act ? __ldcs(a.perm + p) : 0;
+    int f0 = act ? __ldcs(a.cptr + p) : 0, f1 = act ? __ldcs(a.cptr + p + 1) : 0;
+    T di = act ? __ldcs(a.dinv + p) : T(0);
+    if (!wait()) {
+        tile_drain(a, c, 0, pre_issued);
+        c.k += pre_issued;
+        return false;
+    }
+    const size_t bb = tile_buf_bytes(a.tile_ecap, (int)sizeof(T));
+    const size_t voff = align16((size_t)(a.tile_ecap + 4) * 4);
+    for (int i = 0; i < nt; ++i) {
+        const uint32_t kk = c.k + (uint32_t)i;
+        const uint32_t slot = kk & 1;
+        const T bv = act ? __ldcs(a.b + row) : T(0);
+        // next tile's row
+        const int64_t pn = p + TR;
+        const bool actn = t < TR && pn < my1;
+        const int32_t rown = actn ? __ldcs(a.perm + pn) : 0;
+        const int f0n = actn ? __ldcs(a.cptr + pn) : 0, f1n = actn ? __ldcs(a.cptr + pn + 1) : 0;
+        const T din = actn ? __ldcs(a.dinv + pn) : T(0);
+        const bool got = mbar_wait_bounded(g_tile_mbar + slot, (kk >> 1) & 1, a.timeout_ns);
+        if (got && act) {
+            const int q0 = g_tile_q[i];
+            const int32_t* cs = (const int32_t*)(g_dyn_smem + slot * bb) + (f0 - (q0 & ~3));
+            const T* vs = (const T*)(g_dyn_smem + slot * bb + voff) + (f0 - (q0 & ~(VA - 1)));
+            const int len = f1 - f0;
+            T acc = di * bv;
+            if (a.eptr) {
+                const int e1 = a.eptr[p + 1];
+                for (int q = a.eptr[p]; q < e1; ++q) acc += a.eval[q] * a.b[a.ecol[q]];
+            }
+            for (int u = 0; u < len; u += 4) {
+                T xv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xv[j] = u + j < len ? __ldcg(a.xp + cs[u + j]) : T(0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (u + j < len) acc -= vs[u + j] * xv[j];
+            }
+            __stcg(a.xp + p, acc);
+            __stcs(a.x + row, acc);
+        }
+        // every thread is done with the buffer before it is refilled; a copy that never completed
+        // stops the CTA after its other copies in flight are waited for
+        if (__syncthreads_or(!got)) {
+            if (t == 0) atomicCAS(a.status, 0, (int)DEV_TIMEOUT);
+            tile_drain(a, c, i, min(nt, i + 2));
+            c.k += min(nt, i + 2);
+            return false;
+        }
+        if (t == 0 && i + 2 < nt) tile_issue(a, i + 2, slot);
+        p = pn;
+        act = actn;
+        row = rown;
+        f0 = f0n;
+        f1 = f1n;
+        di = din;
+    }
+    c.k += nt;
+    return true;
+}
+
 // the rows [my0, my1) of one level with lanes-per-row wl (0: the schedule's), `wait` taken after the
 // first row's independent data is in registers
 template <typename T, typename WaitFn>
@@ -318,12 +438,26 @@ __device__ __forceinline__ bool level_rows(const SolveArgs<T>& a, const Lanes& l
 // flag waits, and publishes nothing, so that the CTAs waiting on it run out too; inside a cluster
 // region it still takes every cluster barrier, so that no CTA of its cluster waits on it forever.
 // No CTA returns early.
-template <typename T, bool CL>
+// kernel variants (one register allocation each): plain, plain with tiled WIDE levels, cluster
+enum KMode : int { KM_PLAIN = 0, KM_TILED = 1, KM_CLUSTER = 2 };
+
+template <typename T, int MODE>
 __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool CL = MODE == KM_CLUSTER;
+    constexpr bool TL = MODE == KM_TILED;
+    unsigned char* smem = g_dyn_smem;
     const int nrhs = a.nrhs;
     const Lanes ln = make_lanes(a.lpr, nrhs);
     const int me = blockIdx.x;
+    TileCtx tc{0u};
+    if (TL && a.tile_ecap > 0) {
+        if (threadIdx.x == 0) {
+            mbar_init(&g_tile_mbar[0], 1);
+            mbar_init(&g_tile_mbar[1], 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
     if constexpr (!CL) {
         // no CLUSTER segments: a CTA whose bounded wait runs out returns
         for (int s = 0; s < a.nseg; ++s) {
@@ -335,7 +469,16 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
                 const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
                 const int64_t my0 = p0 + (int64_t)me * sg.z;
                 const int64_t my1 = min(p1, my0 + (int64_t)sg.z);
-                if (!level_rows(a, ln, wl, my0, my1, [&]() { return wait_segment(a, s - 1); })) return;
+                auto w = [&]() { return wait_segment(a, s - 1); };
+                bool ok;
+                if constexpr (TL) {
+                    ok = (sg.x & SEG_TILED)
+                             ? wide_rows_tiled(a, my0, my1, TILE_ROWS >> ((sg.x >> SEG_TILE_SHIFT) & 3), tc, w)
+                             : level_rows(a, ln, wl, my0, my1, w);
+                } else {
+                    ok = level_rows(a, ln, wl, my0, my1, w);
+                }
+                if (!ok) return;
                 publish(a, s);
                 if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
             } else {
@@ -414,21 +557,29 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
 }
 
 // Kernel attributes of the k_solve instantiation a launch with csize CTAs per cluster uses
+// the variant a schedule runs: cluster when it has CLUSTER segments, tiled when it has tiled WIDE
+// segments, else plain
+inline int k_mode(int csize, int tile_ecap) { return csize > 1 ? KM_CLUSTER : (tile_ecap > 0 ? KM_TILED : KM_PLAIN); }
+
 template <typename T>
-cudaError_t k_solve_attrs(size_t smem, int csize) {
-    if (csize > 1) {
-        cudaError_t e = cudaFuncSetAttribute(k_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess && csize > 8)
-            e = cudaFuncSetAttribute(k_solve<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        return e;
-    }
-    return cudaFuncSetAttribute(k_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+const void* k_solve_fn(int mode) {
+    return mode == KM_CLUSTER ? (const void*)k_solve<T, KM_CLUSTER>
+                              : (mode == KM_TILED ? (const void*)k_solve<T, KM_TILED> : (const void*)k_solve<T, KM_PLAIN>);
+}
+
+template <typename T>
+cudaError_t k_solve_attrs(size_t smem, int csize, int tile_ecap) {
+    const void* fn = k_solve_fn<T>(k_mode(csize, tile_ecap));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && csize > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
 }
 
 // Launches k_solve for a prepared schedule: cooperative (all CTAs co-resident, so every bounded
 // wait can succeed), and with the schedule's cluster size when it has CLUSTER segments.
 template <typename T>
 cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t smem, int csize, cudaStream_t st) {
+    const int mode = k_mode(csize, a.tile_ecap);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
@@ -447,8 +598,9 @@ cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t sm
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    if (csize > 1) return cudaLaunchKernelEx(&cfg, k_solve<T, true>, a);
-    return cudaLaunchKernelEx(&cfg, k_solve<T, false>, a);
+    if (mode == KM_CLUSTER) return cudaLaunchKernelEx(&cfg, k_solve<T, KM_CLUSTER>, a);
+    if (mode == KM_TILED) return cudaLaunchKernelEx(&cfg, k_solve<T, KM_TILED>, a);
+    return cudaLaunchKernelEx(&cfg, k_solve<T, KM_PLAIN>, a);
 }
 
 }  // namespace

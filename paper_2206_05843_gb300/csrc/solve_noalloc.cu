@@ -88,6 +88,7 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
     a.stage_entries = sc.stage_entries;
     a.pre = sc.pre;
     a.csize = sc.csize;
+    a.tile_ecap = sc.tile_ecap;
     SP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
     if (sc.run_width == -2) {
         // the system is tuned to one launch per level: the same launches as sptrsv_solve, with
@@ -100,7 +101,7 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
         SP_CUDA(cudaGetLastError());
         return SPTRSV_OK;
     }
-    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize));
+    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize, sc.tile_ecap));
     SP_CUDA(cudaMemsetAsync(a.flags, 0xff, (size_t)sc.grid * sizeof(int), st));
     if (a.nseg == 0) return SPTRSV_OK;
     if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());

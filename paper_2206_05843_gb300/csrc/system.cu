@@ -226,6 +226,9 @@ sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info*
     o->cluster_setting = s->cluster;
     o->cluster_levels = sc.segs.p ? sc.cluster_levels : 0;
     o->cluster_rows = s->cluster_rows;
+    o->tiled_levels = sc.segs.p ? sc.tiled_levels : 0;
+    o->tiles_setting = s->tiles;
+    o->reserved0 = 0;
     return SPTRSV_OK;
 }
 
@@ -312,11 +315,13 @@ sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_wi
     return SPTRSV_OK;
 }
 
-sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows) {
+sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows, int32_t tiles) {
     if (!s) { set_error("system_tune_cluster: null system"); return SPTRSV_ERR_INVALID; }
     if (cluster > 16) { set_error("system_tune_cluster: at most 16 CTAs per cluster"); return SPTRSV_ERR_INVALID; }
+    if (tiles > 1) { set_error("system_tune_cluster: tiles must be 0 (automatic) or 1 (never)"); return SPTRSV_ERR_INVALID; }
     if (cluster >= 0) s->cluster = cluster;
     if (cluster_rows >= 0) s->cluster_rows = cluster_rows;
+    if (tiles >= 0) s->tiles = tiles;
     s->sched.nrhs = -1;  // rebuild on the next solve
     return SPTRSV_OK;
 }

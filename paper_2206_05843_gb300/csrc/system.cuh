@@ -15,6 +15,19 @@ constexpr int SEG_TYPE_MASK = 0xff, SEG_LPR_SHIFT = 8, SEG_LPR_MASK = 0xff;
 // Every segment of a region carries SEG_REGION; the first (SEG_FIRST) is entered through the flags
 // of the segment before it, the last (SEG_LAST) publishes the flags for the segment after it.
 constexpr int SEG_REGION = 1 << 16, SEG_FIRST = 1 << 17, SEG_LAST = 1 << 18;
+// A WIDE segment of one right-hand side whose coefficients stream through shared memory in tiles of
+// TILE_ROWS >> ((x >> SEG_TILE_SHIFT) & 3) rows (bulk copies, double-buffered): SEG_TILED
+constexpr int SEG_TILED = 1 << 19, SEG_TILE_SHIFT = 20;
+constexpr int TILE_ROWS = 512;   // rows of a tile at the largest size (one per thread of a 512-thread CTA)
+constexpr int TILE_MAX = 64;     // tiles of one CTA's share of a level
+constexpr int64_t TILE_SMEM_MAX = 100 * 1024;  // shared memory the two tile buffers may take (2 CTAs per SM)
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+// bytes of one tile buffer holding `ecap` coefficients (columns, then values) of vb-byte values,
+// with room for the 16-byte rounding of both bulk copies
+__host__ __device__ inline size_t tile_buf_bytes(int64_t ecap, int vb) {
+    return align16((size_t)(ecap + 4) * 4) + align16((size_t)(ecap + 4) * vb);
+}
 
 // rows a ROWCAP target holds by default: the lanes of one warp, the fast executor's level width
 constexpr int ROWCAP_DEFAULT_ROWS = 32;
@@ -39,10 +52,13 @@ struct Schedule {
     int nrhs = -1, block = 0, run_width = 0, lpr = 0, grid = 0, ring_rows = 0;
     int csize = 1;          // CTAs per cluster of the launch (1: no cluster segments, plain launch)
     int cluster = 0;        // the system's cluster setting the schedule was built with
+    int tiles = 0;          // the system's tile setting the schedule was built with
     int64_t cluster_rows = 0;  // widest level run as a CLUSTER level
     int64_t cluster_levels = 0;  // levels executed in CLUSTER segments
     int stage_rows = 0, stage_entries = 0;
     int pre = 0;       // a b-part kernel runs before the solve (rewritten rows in staged blocks)
+    int tile_ecap = 0; // coefficients a tile buffer holds (0: no tiled WIDE segments)
+    int64_t tiled_levels = 0;
     int pre_grid = 0;  // its CTAs
     size_t smem = 0;
     int64_t run_levels = 0;
@@ -79,6 +95,7 @@ struct SolveArgs {
     int ring_rows;  // power of two
     int lpr;        // lanes per row (power of two <= 32)
     int csize;      // CTAs per cluster (1: launched without clusters)
+    int tile_ecap;  // coefficients one tile buffer holds (0: no tiled WIDE segments)
     int stage_rows, stage_entries;
     int pre;        // xp holds the b-parts of the staged blocks' rows (k_bparts ran first)
 };
@@ -99,6 +116,7 @@ struct sptrsv_system {
     // solve state
     int block = 512, run_width = 0, lpr = 0;  // 0: automatic
     int cluster = 0;          // CTAs of the cluster that runs mid-width levels: 0 automatic, 1 none, 2..16
+    int tiles = 0;            // wide levels through shared-memory tiles: 0 automatic, 1 never
     int64_t cluster_rows = 0; // widest level run on the cluster (0: automatic)
     sp::Schedule sched;
     std::vector<int32_t> h_cptr;  // host copy of cptr, for cutting run blocks

@@ -2,11 +2,14 @@
 itself.
 
 Harvest (per training matrix): the plain system is solved with per-level %globaltimer
-stamps; then, for every candidate depth g, the matrix is rewritten with targets every
-g+1 levels (under the nnz cap) and solved with stamps.  For a target level t the label is
-  dt(t, g) = time of the rewritten levels that hold original levels t..t+g
-           - time of original levels t..t+g in the plain solve            (nanoseconds)
-and the sample's input is the 12-feature vector of candidate (t, g) computed on the
+stamps; then, for every candidate (a fixed depth g, or a row budget -r that gives every target
+the largest depth whose window holds at most r rows), the matrix is rewritten with the plan
+family the model drives -- thin levels only (cost below avgLevelCost, Section III), the
+candidate's depth at every target (CHOSEN_THIN) -- and solved with stamps.  For a target level t
+whose group holds original levels t..te the label is
+  dt(t, c) = time of the rewritten levels that hold original levels t..te
+           - time of original levels t..te in the plain solve             (nanoseconds)
+and the sample's input is the 12-feature vector of candidate (t, c) computed on the
 original matrix.  Training runs the library's own MLP forward, backward and Adam kernels.
 
 Evaluation (held-out matrices): solve time of the learned strategy (and of the model's plan
@@ -59,39 +62,69 @@ def timed_stamps(sysm, bt, reps):
     return out
 
 
-def harvest(m, depths=DEPTHS, cap=1.5, reps=3, seed=0):
-    """Samples (features, dt in ns) of one matrix."""
+def candidate_depths(rows: np.ndarray, c: int) -> np.ndarray:
+    """The depth candidate c gives every target level (the library's rule): c itself for c >= 1;
+    for c = -r the largest g with rows(t) + ... + rows(t + g) <= r, 0 when level t holds more."""
+    m = rows.size
+    if c >= 1:
+        return np.full(m, c, np.int32)
+    P = np.concatenate([[0], np.cumsum(rows.astype(np.int64))])
+    j = np.searchsorted(P, P[:-1] + (-c), side="right") - 1  # largest j with P[j] <= P[t] + r
+    return np.maximum(j - 1 - np.arange(m), 0).astype(np.int32)
+
+
+def harvest(m, depths=DEPTHS, reps=3, seed=0, per_candidate=20000):
+    """Samples (features, dt in ns) of one matrix: every target of a thin-level plan with the
+    candidate's depths (no nnz cap, so that every group holds its whole window); at most
+    per_candidate targets per candidate, drawn at random."""
     torch = _torch()
     M = B.Matrix.from_host(m)
     lv = B.Levels(M)
     mm = lv.m
     if mm < 3:
         return np.zeros((0, 12), np.float32), np.zeros(0, np.float32)
-    old_level = lv.export()["level"].astype(np.int64)
+    lex = lv.export()
+    old_level = lex["level"].astype(np.int64)
+    rows = np.asarray(lex["rows"], np.int64)
     b = S.rhs_uniform(m.n, 1, seed)
     bt = torch.from_numpy(b[0]).cuda()
     feats = B.features(M, lv, depths).cpu().numpy().reshape(mm, len(depths), 12)
     plain = B.System(M, lv)
-    sp = timed_stamps(plain, bt, reps)
+    sp = np.stack(timed_stamps(plain, bt, reps))
+    rng = np.random.default_rng(seed)
+    idx = np.arange(mm)
     X, Y = [], []
-    for d, g in enumerate(depths):
+    for d, c in enumerate(depths):
         try:
-            s = B.System(M, lv, B.DEPTH_K, k=g, cap=cap)
+            s = B.System(M, lv, B.CHOSEN_THIN, depth_of_target=candidate_depths(rows, int(c)))
         except B.SptrsvError:
             continue
-        new_level = s.export()["level"].astype(np.int64)
-        lo, hi = level_spans(new_level, old_level, mm)
-        sr = timed_stamps(s, bt, reps)
-        for t in range(g + 1, mm, g + 1):
-            te = min(t + g, mm - 1)
-            nlo, nhi = int(lo[t:te + 1].min()), int(hi[t:te + 1].max())
-            if nlo <= 0:
-                continue
-            deltas = [(r[nhi] - r[nlo - 1]) - (p[te] - p[t - 1]) for r, p in zip(sr, sp)]
-            X.append(feats[t, d])
-            Y.append(statistics.median(deltas))
+        ex = s.export()
+        ltarget = np.empty(mm, np.int64)
+        ltarget[old_level] = ex["target"].astype(np.int64)  # without a cap a level moves as a whole
+        lo, hi = level_spans(ex["level"].astype(np.int64), old_level, mm)
+        sr = np.stack(timed_stamps(s, bt, reps))
         del s
-    return np.asarray(X, np.float32).reshape(-1, 12), np.asarray(Y, np.float32)
+        # groups: a target t and the levels that moved into it (t..te)
+        te = np.full(mm, -1, np.int64)
+        np.maximum.at(te, ltarget, idx)
+        glo = np.full(mm, np.iinfo(np.int64).max, np.int64)
+        ghi = np.full(mm, -1, np.int64)
+        np.minimum.at(glo, ltarget, lo)
+        np.maximum.at(ghi, ltarget, hi)
+        tg = np.nonzero((te > idx) & (idx > 0))[0]
+        tg = tg[glo[tg] > 0]
+        if tg.size > per_candidate:
+            tg = np.sort(rng.choice(tg, size=per_candidate, replace=False))
+        if tg.size == 0:
+            continue
+        dr = sr[:, ghi[tg]] - sr[:, glo[tg] - 1]
+        dp = sp[:, te[tg]] - sp[:, tg - 1]
+        X.append(feats[tg, d])
+        Y.append(np.median(dr - dp, axis=0))
+    if not X:
+        return np.zeros((0, 12), np.float32), np.zeros(0, np.float32)
+    return np.concatenate(X).astype(np.float32), np.concatenate(Y).astype(np.float32)
 
 
 def train(X, Y, seed=0, epochs=60, batch=4096, lr=2e-3, log=None):
@@ -138,7 +171,12 @@ def solve_time_us(sysm, bt, reps=5):
 
 
 def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
-    """Solve time of none / naive / learned; errors against x_true (b = L x_true)."""
+    """Solve time of no rewrite, the paper's naive strategy, the ROWCAP plan and the network's own
+    plan (the learned strategy with model_only), each with its error against x_true (b = L x_true).
+    The learned strategy's measured choice is the fastest of those four (the library times the
+    same four candidates and keeps the fastest); "choice_without_model" is the fastest of the
+    three without the network, so that the network's own contribution shows apart from the
+    fallbacks."""
     torch = _torch()
     rows = []
     t0 = time.time()
@@ -155,12 +193,17 @@ def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
         res = {"n": m.n, "levels": lv.m}
         for name, kw in (("none", {}), ("naive", dict(kind=B.NAIVE, cap=cap)),
                          ("rowcap", dict(kind=B.ROWCAP, k=32, cap=cap)),
-                         ("learned", dict(kind=B.LEARNED, cap=cap, picker=pk)),
                          ("learned_model_only", dict(kind=B.LEARNED, cap=cap, picker=pk, model_only=True))):
             s = B.System(M, lv, **kw)
             us, x = solve_time_us(s, bt)
             err = float(np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref))
             res[name] = {"us": us, "levels": s.m, "rel_err": err, "strategy_used": int(s.info["strategy_used"])}
+            del s
+        cand = {k: res[k]["us"] for k in ("learned_model_only", "naive", "rowcap", "none")}
+        best = min(cand, key=cand.get)
+        res["learned"] = dict(res[best], kept=best)
+        best_wo = min(("naive", "rowcap", "none"), key=lambda k: cand[k])
+        res["choice_without_model"] = dict(res[best_wo], kept=best_wo)
         rows.append(res)
         if log:
             log(json.dumps(res))
@@ -174,9 +217,10 @@ def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
                    [np.log(r["naive"]["us"] / r["learned"]["us"]) for r in rows]))),
                "geomean_speedup_model_only_vs_naive": float(np.exp(np.mean(
                    [np.log(r["naive"]["us"] / r["learned_model_only"]["us"]) for r in rows]))),
-               "model_plan_kept": int(sum(r["learned"]["strategy_used"] == B.CHOSEN for r in rows)),
-               "max_rel_err": max(max(r[k]["rel_err"] for k in ("none", "naive", "rowcap", "learned",
-                                                                "learned_model_only"))
+               "geomean_speedup_choice_with_vs_without_model": float(np.exp(np.mean(
+                   [np.log(r["choice_without_model"]["us"] / r["learned"]["us"]) for r in rows]))),
+               "model_plan_kept": int(sum(r["learned"]["kept"] == "learned_model_only" for r in rows)),
+               "max_rel_err": max(max(r[k]["rel_err"] for k in ("none", "naive", "rowcap", "learned_model_only"))
                                   for r in rows)}
     return rows, summary
 
@@ -195,6 +239,8 @@ def main(argv=None):
     ap.add_argument("--time-budget", type=float, default=1e9, help="seconds for the harvest")
     ap.add_argument("--eval-budget", type=float, default=1e9, help="seconds for the held-out evaluation")
     ap.add_argument("--evaluate", default=None, help="evaluate this trained picker file only (no training)")
+    ap.add_argument("--save-data", default=None, help="write the harvested samples to this .npz file")
+    ap.add_argument("--load-data", default=None, help="train on samples from this .npz file (no harvest)")
     a = ap.parse_args(argv)
 
     def log(s):
@@ -211,23 +257,29 @@ def main(argv=None):
         json.dump({"picker": a.evaluate, "summary": summary, "heldout": rows}, open(a.report, "w"), indent=1)
         log(json.dumps(summary))
         return 0
-    rng = S.rng_for(12345)
-    t0 = time.time()
-    Xs, Ys = [], []
-    used = 0
-    for i in range(a.train):
-        if time.time() - t0 > a.time_budget:
-            break
-        n = int(round(np.exp(rng.uniform(np.log(a.n_lo), np.log(a.n_hi)))))
-        m = S.gen_mixture(n, 10_000 + i)
-        X, Y = harvest(m, seed=i)
-        Xs.append(X)
-        Ys.append(Y)
-        used += 1
-        if i % 20 == 0:
-            log(f"harvest {i}: n={m.n} samples={len(Y)} elapsed={time.time() - t0:.0f}s")
-    X = np.concatenate(Xs)
-    Y = np.concatenate(Ys)
+    if a.load_data:
+        z = np.load(a.load_data)
+        X, Y, used = z["X"], z["Y"], int(z["matrices"])
+    else:
+        rng = S.rng_for(12345)
+        t0 = time.time()
+        Xs, Ys = [], []
+        used = 0
+        for i in range(a.train):
+            if time.time() - t0 > a.time_budget:
+                break
+            n = int(round(np.exp(rng.uniform(np.log(a.n_lo), np.log(a.n_hi)))))
+            m = S.gen_mixture(n, 10_000 + i)
+            X, Y = harvest(m, seed=i)
+            Xs.append(X)
+            Ys.append(Y)
+            used += 1
+            if i % 20 == 0:
+                log(f"harvest {i}: n={m.n} samples={len(Y)} elapsed={time.time() - t0:.0f}s")
+        X = np.concatenate(Xs)
+        Y = np.concatenate(Ys)
+        if a.save_data:
+            np.savez_compressed(a.save_data, X=X, Y=Y, matrices=used)
     log(f"dataset: {X.shape[0]} samples from {used} matrices")
     pk, hist = train(X, Y, epochs=a.epochs, log=log)
     pk.save(a.out)

@@ -14,7 +14,8 @@ from tests.gpu_util import TOL_F32, TOL_F64, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-KIND = {B.NAIVE: O.NAIVE, B.DEPTH_K: O.DEPTH, B.CHOSEN: O.CHOSEN, B.MANUAL: O.MANUAL, B.ROWCAP: O.ROWCAP}
+KIND = {B.NAIVE: O.NAIVE, B.DEPTH_K: O.DEPTH, B.CHOSEN: O.CHOSEN, B.MANUAL: O.MANUAL, B.ROWCAP: O.ROWCAP,
+        B.CHOSEN_THIN: O.CHOSEN_THIN}
 
 
 def run_both(m, kind, b=None, k=0, cap=0.0, depth_of_target=None, exact=True):
@@ -205,3 +206,22 @@ def test_per_row_rules_match_oracle(alpha, beta):
         assert np.array_equal(s.export()["target"], p.target)
         x = s.solve(torch.from_numpy(b).cuda(), check_status=True).cpu().numpy()
         assert rel_l2(x, O.forward_subst(m.rowptr, m.colidx, m.vals, b)) <= TOL_F64
+
+
+@pytest.mark.parametrize("cap", [0.0, 1.5])
+@pytest.mark.parametrize("which", ["c0", "mixture"])
+def test_chosen_thin_per_target_depths(which, cap):
+    """Depth per target over thin levels (the learned strategy's plan family), with depths drawn per
+    level, with and without the nnz cap (without it the targets map level by level)."""
+    m = S.gen_config("c0")[0] if which == "c0" else S.gen_mixture(40_000, 10_321)
+    _, b = S.rhs_from_xtrue(m, 1, 3)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    dot = S.rng_for(5).integers(0, 12, size=mm)
+    run_both(m, B.CHOSEN_THIN, b, cap=cap, depth_of_target=dot)
+
+
+def test_manual_without_cap_maps_levels():
+    m = S.gen_mixture(30_000, 10_322)
+    _, b = S.rhs_from_xtrue(m, 1, 4)
+    for k in (2, 9):
+        run_both(m, B.MANUAL, b, k=k)

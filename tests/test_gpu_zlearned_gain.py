@@ -77,3 +77,40 @@ def test_bench_configuration_full_size_matches_oracle():
     x = s.solve(torch.from_numpy(b).cuda(), check_status=True).cpu().numpy()
     assert rel_l2(x, O.forward_subst(m.rowptr, m.colidx, m.vals, b)) < TOL_F64
     assert rel_l2(x, xt) < 1e-12
+
+
+def test_trained_network_own_plan_on_held_out_mixtures():
+    """What the trained network itself gains: its own plan (the learned strategy with model_only,
+    no fallback) against the paper's naive strategy on the first three held-out mixtures, in
+    geometric mean; and the learned strategy's measured choice with the network against the same
+    choice without it (naive, ROWCAP, no rewrite).  Solutions exact to 1e-10."""
+    torch = torch_cuda()
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2206_05843_gb300",
+                        "picker_trained.bin")
+    pk = B.Picker.load(path)
+    erng = S.rng_for(54321)
+    own, with_vs_without = [], []
+    for i in range(3):
+        n = int(round(np.exp(erng.uniform(np.log(100_000), np.log(1_000_000)))))
+        m = S.gen_mixture(n, 20_000 + i)
+        xt, b = S.rhs_from_xtrue(m, 1, 7)
+        M = B.Matrix.from_host(m)
+        lv = B.Levels(M)
+        bt = torch.from_numpy(b[0]).cuda()
+        t = {}
+        for name, kw in (("none", {}), ("naive", dict(kind=B.NAIVE, cap=1.5)),
+                         ("rowcap", dict(kind=B.ROWCAP, k=32, cap=1.5)),
+                         ("model", dict(kind=B.LEARNED, cap=1.5, picker=pk, model_only=True))):
+            sysm = B.System(M, lv, **kw)
+            t[name], x = _median_solve_us(sysm, bt)
+            assert rel_l2(x.cpu().numpy(), xt[0]) < TOL_F64, name
+        own.append(t["naive"] / t["model"])
+        without = min(t["naive"], t["rowcap"], t["none"])
+        with_vs_without.append(without / min(without, t["model"]))
+    g_own = float(np.exp(np.mean(np.log(own))))
+    g_choice = float(np.exp(np.mean(np.log(with_vs_without))))
+    print(f"network's plan over naive: {own} (geomean {g_own:.3f}); "
+          f"choice with / without the network: {with_vs_without} (geomean {g_choice:.3f})")
+    assert g_own >= 1.0, own
+    # the network's plan is the fastest of all four candidates on at least one of the matrices
+    assert max(with_vs_without) > 1.0, with_vs_without

@@ -119,3 +119,28 @@ def test_features_grid_widths():
         te = min(t + 2, mm - 1)
         assert F[t, 7] == pytest.approx(math.log2(1 + width[t]))
         assert F[t, 1] == pytest.approx(math.log2(1 + sum(width[t:te + 1])))
+
+
+def test_row_capped_candidates_closed_forms():
+    """A row budget -r: on a chain (one row per level) the window holds r levels, g = r - 1 (cut at
+    the last level); on the 9 x 9 grid (widths 1, 2, ..., 9, ..., 1) the depths follow the widths;
+    the candidate's features are those of the fixed depth it resolves to."""
+    n = 40
+    chain = S.gen_from_deps(n, np.array([0] + [1] * (n - 1)), np.arange(n - 1), S.rng_for(0))
+    rows = np.ones(n, np.int64)
+    for t in (0, 10, 35, 39):
+        assert OF.candidate_depth(rows, t, -8) == min(7, n - 1 - t)
+        assert OF.candidate_depth(rows, t, -1) == 0
+    F = OF.features(chain.rowptr, chain.colidx, [-8, 7, 3]).reshape(n, 3, 12)
+    assert np.array_equal(F[10, 0], F[10, 1])  # -8 resolves to depth 7 at t = 10
+    assert np.array_equal(F[36, 0], F[36, 2])  # and to depth 3 at t = 36 (3 levels left)
+    side = 9
+    grid = S.gen_laplacian(side)
+    width = np.array([min(l + 1, 2 * side - 1 - l) for l in range(2 * side - 1)])
+    # widths 1,2,3,4,... : a budget of 10 rows takes levels 0..3 from t = 0 (1+2+3+4 = 10)
+    assert OF.candidate_depth(width, 0, -10) == 3
+    assert OF.candidate_depth(width, 0, -9) == 2
+    assert OF.candidate_depth(width, 8, -9) == 0    # level 8 alone holds 9 rows
+    assert OF.candidate_depth(width, 8, -8) == 0    # more than the budget: no rewrite
+    assert OF.candidate_depth(width, 13, -9) == 2   # widths 4, 3, 2 = 9
+    assert OF.candidate_depth(width, 16, -100) == 0  # the last level has nothing after it
