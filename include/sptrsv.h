@@ -155,6 +155,11 @@ typedef struct {
                                       and the fastest is kept -- the paper's strategy, the executor-shaped plan and
                                       no rewrite are the fallbacks, the measured solve time decides; 1 = the
                                       picker's plan only */
+    int32_t walk_parts;            /* planner walks (NAIVE, MANUAL, ROWCAP, CHOSEN(_THIN), LEARNED; with a cap or per-row
+                                      rules): <= 1 one walk over all levels; P > 1 starts the walk at the beginning of
+                                      each of P equal level ranges, one warp per range at the same time (Section III:
+                                      the rewriting can also start at the end of the graph; P = 2 is both ends), the
+                                      cap's allowance shared by the ranges in proportion to their entries */
 } sptrsv_strategy;
 
 /* Plans the rewrite with the strategy, rewrites the chosen rows (substitution of every

@@ -62,6 +62,9 @@ def _load():
         lib.orc_plan.restype = C.c_int
         lib.orc_plan_rules.argtypes = [i64, vp, vp, vp, i32, C.c_int, i32, dbl, dbl, vp, vp, i32, i64, vp, vp, vp]
         lib.orc_plan_rules.restype = C.c_int
+        lib.orc_plan_parts.argtypes = [i64, vp, vp, vp, i32, C.c_int, i32, dbl, dbl, vp, vp, i32, i64, i32, vp, vp,
+                                       vp]
+        lib.orc_plan_parts.restype = C.c_int
         lib.orc_rewrite.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.orc_rewrite.restype = vp
         lib.orc_system_free.argtypes = [vp]
@@ -175,9 +178,10 @@ class Plan:
 
 
 def plan(rowptr, colidx, level, m, kind: int, k: int = 0, avg: float = 0.0, cap: float = 0.0,
-         injected_cost=None, depth_of_target=None, alpha: int = 0, beta: int = 0) -> Plan:
+         injected_cost=None, depth_of_target=None, alpha: int = 0, beta: int = 0, parts: int = 1) -> Plan:
     """The Section III planner (NAIVE / DEPTH / CHOSEN / MANUAL / CHOSEN_THIN / ROWCAP), with the per-row rules of
-    Section III.A (alpha: fewer dependencies than alpha; beta: dependency spread below beta)."""
+    Section III.A (alpha: fewer dependencies than alpha; beta: dependency spread below beta); parts > 1 starts the
+    walk at the beginning of every one of `parts` equal level ranges (2: from both ends, Section III)."""
     rp, ci, lv = _i32(rowptr), _i32(colidx), _i32(level)
     n = rp.size - 1
     tgt = np.empty(max(n, 1), np.int32)
@@ -185,9 +189,9 @@ def plan(rowptr, colidx, level, m, kind: int, k: int = 0, avg: float = 0.0, cap:
     info = np.zeros(6, np.int64)
     inj = None if injected_cost is None else np.ascontiguousarray(injected_cost, dtype=np.int64)
     dot = None if depth_of_target is None else _i32(depth_of_target)
-    rc_ = _load().orc_plan_rules(n, _p(rp), _p(ci), _p(lv), int(m), int(kind), int(k), float(avg), float(cap),
+    rc_ = _load().orc_plan_parts(n, _p(rp), _p(ci), _p(lv), int(m), int(kind), int(k), float(avg), float(cap),
                                  None if inj is None else _p(inj), None if dot is None else _p(dot),
-                                 int(alpha), int(beta), _p(tgt), _p(rc), _p(info))
+                                 int(alpha), int(beta), int(parts), _p(tgt), _p(rc), _p(info))
     if rc_ != 0:
         raise MemoryError("oracle planner allocation failed")
     return Plan(tgt[:n].copy(), rc[:n].copy(), int(info[0]), int(info[1]), int(info[2]), int(info[3]),

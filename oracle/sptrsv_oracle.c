@@ -228,6 +228,11 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
                    const int64_t* injected_cost, const int32_t* depth_of_target, int32_t alpha,
                    int64_t beta, int32_t* target, int64_t* row_cost, int64_t* info);
 
+int orc_plan_parts(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int32_t* level,
+                   int32_t m, int kind, int32_t k, double avg_override, double cap_ratio,
+                   const int64_t* injected_cost, const int32_t* depth_of_target, int32_t alpha,
+                   int64_t beta, int32_t parts, int32_t* target, int64_t* row_cost, int64_t* info);
+
 int orc_plan(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int32_t* level,
              int32_t m, int kind, int32_t k, double avg_override, double cap_ratio,
              const int64_t* injected_cost, const int32_t* depth_of_target,
@@ -245,6 +250,23 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
                    int32_t m, int kind, int32_t k, double avg_override, double cap_ratio,
                    const int64_t* injected_cost, const int32_t* depth_of_target, int32_t alpha,
                    int64_t beta, int32_t* target, int64_t* row_cost, int64_t* info) {
+    return orc_plan_parts(n, rowptr, colidx, level, m, kind, k, avg_override, cap_ratio, injected_cost,
+                          depth_of_target, alpha, beta, 1, target, row_cost, info);
+}
+
+/* The walk started at several places at once (Section III: since emptied levels are removed only
+ * when the process ends, the rewriting can also start at the end of the graph while it runs from
+ * the beginning).  The levels are cut into `parts` consecutive ranges, range i = levels
+ * [i*m/parts, (i+1)*m/parts); every range is walked by the rule above from a fresh start (no
+ * target carried in), ranges in ascending order.  parts = 2 is the walk from both ends.  The nnz
+ * cap's allowance, floor(cap*nnz(L)) - nnz(L), is shared: range i may add at most
+ * allowance * nnz(rows of range i) / nnz(L) entries (integer division).  Substitution never
+ * reaches below a target, so what a range decides does not depend on the other ranges. */
+int orc_plan_parts(int64_t n, const int32_t* rowptr, const int32_t* colidx, const int32_t* level,
+                   int32_t m, int kind, int32_t k, double avg_override, double cap_ratio,
+                   const int64_t* injected_cost, const int32_t* depth_of_target, int32_t alpha,
+                   int64_t beta, int32_t parts, int32_t* target, int64_t* row_cost, int64_t* info) {
+    if (parts < 1) parts = 1;
     int64_t* lrows = (int64_t*)calloc((size_t)m + 1, sizeof(int64_t));
     int64_t* lcost = (int64_t*)calloc((size_t)m + 1, sizeof(int64_t));
     int64_t* lptr = (int64_t*)calloc((size_t)m + 2, sizeof(int64_t));
@@ -278,13 +300,32 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
     for (int32_t l = 0; l < m; ++l) total_cost += (double)lcost[l];
     double avg = avg_override > 0.0 ? avg_override : (m > 0 ? total_cost / (double)m : 0.0);
     int64_t limit = cap_ratio > 0.0 ? (int64_t)floor(cap_ratio * (double)nnzL) : INT64_MAX;
+    int64_t allowance = limit - nnzL; /* entries the whole plan may add */
     int64_t stored = nnzL; /* nnz(L') + nnz(E explicit rows) */
     int64_t moved = 0, targets = 0;
 
     iset Dn = {0}, En = {0};
     int32_t t = -1;
     int64_t cur = 0;
+    int32_t part = -1;
+    int64_t part_stored = 0, part_limit = INT64_MAX; /* growth of the current range and its share */
     for (int32_t s = 0; s < m; ++s) {
+        if (part + 1 < parts && (int64_t)s == (int64_t)m * (part + 1) / parts) {
+            /* a range starts (the last of several that start here when parts > m: the others are
+             * empty): fresh walk, its share of the cap's allowance */
+            while (part + 1 < parts && (int64_t)s == (int64_t)m * (part + 1) / parts) part++;
+            t = -1;
+            cur = 0;
+            part_stored = 0;
+            if (limit != INT64_MAX) {
+                int64_t z = 0, lend = (int64_t)m * (part + 1) / parts;
+                for (int64_t q = lptr[s]; q < lptr[lend]; ++q) {
+                    int64_t r = byl[q];
+                    z += (int64_t)rowptr[r + 1] - rowptr[r];
+                }
+                part_limit = nnzL > 0 ? allowance * z / nnzL : 0;
+            }
+        }
         int eligible = (kind == ORC_NAIVE || kind == ORC_MANUAL || kind == ORC_CHOSEN_THIN || kind == ORC_ROWCAP)
                            ? ((double)lcost[s] < avg) : 1;
         if (!eligible) { t = -1; continue; }
@@ -319,7 +360,7 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
             int64_t c = injected_cost ? injected_cost[r] : 2 * (int64_t)Dn.len;
             int64_t growth = (int64_t)Dn.len + (int64_t)En.len - (int64_t)D[r].len;
             int fits_cost = (kind == ORC_NAIVE) ? ((double)(cur + c) <= avg) : (kind == ORC_ROWCAP) ? (cur + 1 <= k) : 1;
-            int fits_cap = (stored + growth <= limit);
+            int fits_cap = limit == INT64_MAX || (part_stored + growth <= part_limit);
             int fits_rules = 1;
             if (alpha > 0 && Dn.len >= alpha) fits_rules = 0;
             if (beta > 0 && Dn.len > 1 && (int64_t)Dn.v[Dn.len - 1] - (int64_t)Dn.v[0] >= beta) fits_rules = 0;
@@ -329,6 +370,7 @@ int orc_plan_rules(int64_t n, const int32_t* rowptr, const int32_t* colidx, cons
                 row_cost[r] = c;
                 cur += kind == ORC_ROWCAP ? 1 : c;
                 stored += growth;
+                part_stored += growth;
                 moved++;
                 iset tmp = D[r]; D[r] = Dn; Dn = tmp;
                 tmp = E[r]; E[r] = En; En = tmp;

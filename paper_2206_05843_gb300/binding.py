@@ -59,7 +59,7 @@ class Strategy(C.Structure):
                 ("avg_override", C.c_double), ("growth_guard", C.c_double), ("picker", C.c_void_p),
                 ("depth_of_target_host", C.c_void_p), ("depths_host", C.c_void_p), ("n_depths", C.c_int32),
                 ("injected_cost_dev", C.c_void_p), ("max_deps", C.c_int32), ("max_spread", C.c_int64),
-                ("learned_mode", C.c_int32)]
+                ("learned_mode", C.c_int32), ("walk_parts", C.c_int32)]
 
 
 class SystemInfo(C.Structure):
@@ -261,13 +261,14 @@ class Levels:
 
 
 def strategy(kind=NONE, k=0, cap=0.0, avg=0.0, guard=0.0, picker=None, depth_of_target=None, depths=None,
-             injected_cost=None, alpha=0, beta=0, model_only=False) -> tuple[Strategy, list]:
+             injected_cost=None, alpha=0, beta=0, model_only=False, walk_parts=1) -> tuple[Strategy, list]:
     """Builds an sptrsv_strategy; returns it with the objects that must stay alive."""
     keep = []
     s = Strategy()
     s.kind, s.k, s.nnz_growth_cap, s.avg_override, s.growth_guard = kind, k, cap, avg, guard
     s.max_deps, s.max_spread = alpha, beta
     s.learned_mode = 1 if model_only else 0
+    s.walk_parts = int(walk_parts)
     s.picker = picker.h if picker is not None else None
     if depth_of_target is not None:
         a = np.ascontiguousarray(depth_of_target, dtype=np.int32)

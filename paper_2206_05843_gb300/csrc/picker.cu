@@ -405,7 +405,8 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
     if (sg->learned_mode == 1) {
         sptrsv_system* model = nullptr;
         SP_TRY(rewrite_system(L, lv, 5 /* depth per thin target */, 0, dot.as<int32_t>(), sg->avg_override,
-                              sg->nnz_growth_cap, sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &model, st));
+                              sg->nnz_growth_cap, sg->growth_guard, nullptr, sg->max_deps, sg->max_spread,
+                              sg->walk_parts, &model, st));
         model->strategy_used = SPTRSV_STRATEGY_CHOSEN;
         *out = model;
         return SPTRSV_OK;
@@ -437,7 +438,8 @@ sptrsv_status learned_rewrite(const sptrsv_csr* L, const sptrsv_levels* lvh, con
             } else {
                 rc = rewrite_system(L, lv, kinds[i], kinds[i] == 6 ? ROWCAP_DEFAULT_ROWS : 0,
                                     kinds[i] == 5 ? dot.as<int32_t>() : nullptr, sg->avg_override, sg->nnz_growth_cap,
-                                    sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, &cand[i], ws);
+                                    sg->growth_guard, nullptr, sg->max_deps, sg->max_spread, sg->walk_parts, &cand[i],
+                                    ws);
                 if (rc == SPTRSV_OK && cudaStreamSynchronize(ws) != cudaSuccess) {
                     set_error("learned strategy: candidate plan failed");
                     rc = SPTRSV_ERR_CUDA;

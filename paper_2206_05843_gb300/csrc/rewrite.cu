@@ -96,7 +96,7 @@ struct WalkArgs {
     const int64_t* lcost;
     int kind, k;
     double avg;
-    int64_t limit;
+    const int64_t* part_limit;  // per level range: entries its moves may add (INT64_MAX: no cap)
     const int32_t* dot;  // depth of target (CHOSEN)
     const int64_t* inj;  // injected costs (test hook)
     int alpha;           // per-row rules (Section III.A): dependencies after substitution < alpha
@@ -108,17 +108,25 @@ struct WalkArgs {
     int64_t* e_off;
     int32_t* e_len;
     int32_t* pool;
-    int64_t pool_cap;
-    int64_t* info;  // moved, stored, targets
+    int64_t pool_cap;   // entries of the pool of one level range
+    int64_t* info;  // per level range: moved, entries added, targets
     int* status;
 };
 
-// one warp walks every level in order
+// One warp walks the levels of one range in order: range w = levels [w*m/P, (w+1)*m/P) of P = gridDim.x
+// ranges, from a fresh start (the walk started at several places, Section III; P = 1 is the single
+// walk).  A range only rewrites rows of its own levels, and substitution never reaches below a
+// target, so it reads nothing another range writes that could change its decisions: a dependency
+// in an earlier range sits on a level below the range's targets whatever its own range did.
 __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
     const int lane = threadIdx.x;
+    const int w = blockIdx.x, P = gridDim.x;
+    const int64_t s_begin = a.m * w / P, s_end = a.m * (w + 1) / P;
+    const int64_t limit = a.part_limit[w];
+    int32_t* const pool = a.pool + (int64_t)w * a.pool_cap;
     int t = -1;
-    int64_t cur = 0, stored = a.nnzL, moved = 0, targets = 0, top = 0;
-    for (int64_t s = 0; s < a.m; ++s) {
+    int64_t cur = 0, stored = 0, moved = 0, targets = 0, top = 0;
+    for (int64_t s = s_begin; s < s_end; ++s) {
         const int64_t ls = a.lcost[s];
         const bool eligible = (a.kind == WALK_NAIVE || a.kind == WALK_MANUAL || a.kind == WALK_CHOSEN_THIN ||
                                a.kind == WALK_ROWCAP)
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
                 if (lane == 0) atomicCAS(a.status, 0, (int)DEV_OVERFLOW);
                 return;
             }
-            int32_t* Dp = a.pool + top + off;
+            int32_t* Dp = pool + top + off;
             int32_t* Ep = Dp + ubD;
             int nd = 0, ne = 0;
             if (valid) {
@@ -172,9 +180,9 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
                     if (a.target[j] >= t) {
                         if (a.level[j] != t) {
                             const int64_t o = a.d_off[j];
-                            for (int u = 0; u < a.d_len[j]; ++u) Dp[nd++] = a.pool[o + u];
+                            for (int u = 0; u < a.d_len[j]; ++u) Dp[nd++] = pool[o + u];
                             const int64_t oe = a.e_off[j];
-                            for (int u = 0; u < a.e_len[j]; ++u) Ep[ne++] = a.pool[oe + u];
+                            for (int u = 0; u < a.e_len[j]; ++u) Ep[ne++] = pool[oe + u];
                         } else {
                             for (int64_t u = a.rowptr[j]; u < (int64_t)a.rowptr[j + 1] - 1; ++u) Dp[nd++] = a.colidx[u];
                             Ep[ne++] = j;
@@ -198,7 +206,7 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
             const unsigned badrule = __ballot_sync(0xffffffffu, !rules);
             const int first_bad = badrule ? __ffs(badrule) - 1 : 32;
             const bool pass = (a.kind != WALK_NAIVE || (double)(cur + pc) <= a.avg) && (!rowcap || cur + pc <= a.k) &&
-                              (stored + pg <= a.limit) && lane < first_bad;
+                              (limit == INT64_MAX || stored + pg <= limit) && lane < first_bad;
             const unsigned failmask = __ballot_sync(0xffffffffu, valid && !pass);
             const int first = failmask ? __ffs(failmask) - 1 : 32;
             const int nvalid = (int)(Bn - base < 32 ? Bn - base : 32);
@@ -237,9 +245,9 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
         __syncwarp();
     }
     if (lane == 0) {
-        a.info[0] = moved;
-        a.info[1] = stored;
-        a.info[2] = targets;
+        a.info[3 * w] = moved;
+        a.info[3 * w + 1] = stored;
+        a.info[3 * w + 2] = targets;
     }
 }
 
@@ -255,12 +263,17 @@ __global__ void k_init_walk(int64_t n, const int32_t* rowptr, const int32_t* lev
 // levels for DEPTH and CHOSEN; over thin levels, cost below avgLevelCost, for MANUAL and CHOSEN_THIN,
 // where a level that is not thin keeps its rows and ends the group)
 __global__ void k_level_targets(int64_t m, int kind, int k, const int32_t* dot, const int64_t* lcost, double avg,
-                                int32_t* ltarget) {
+                                int parts, int32_t* ltarget) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const bool thin_only = kind == WALK_MANUAL || kind == WALK_CHOSEN_THIN;
     const bool by_dot = kind == WALK_CHOSEN || kind == WALK_CHOSEN_THIN;
     int64_t t = -1;
+    int w = 0;  // level range (the walk restarts at the first level of every range)
     for (int64_t s = 0; s < m; ++s) {
+        while (w + 1 < parts && s == m * (w + 1) / parts) {
+            ++w;
+            t = -1;
+        }
         if (thin_only && !((double)lcost[s] < avg)) {
             t = -1;
             ltarget[s] = (int32_t)s;
@@ -495,31 +508,48 @@ struct PlanOut {
 
 // plans targets[n] (device) for the given walk kind; returns planner bookkeeping
 sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int k, const int32_t* dot_dev,
-                           double avg, double cap, const int64_t* inj, int alpha, int64_t beta, int32_t* target,
-                           PlanOut& po, cudaStream_t st) {
+                           double avg, double cap, const int64_t* inj, int alpha, int64_t beta, int parts,
+                           int32_t* target, PlanOut& po, cudaStream_t st) {
     const int64_t n = L->n, m = lv.m;
     // the row walk is needed where the rows decide (cost or row budget, the nnz cap, the per-row rules)
     const bool walk = kind == WALK_NAIVE || kind == WALK_ROWCAP || cap > 0 || inj || alpha > 0 || beta > 0;
     if (!walk) {
         Scratch lt;
         SP_TRY(lt.alloc(std::max<int64_t>(1, m) * sizeof(int32_t), st));
-        k_level_targets<<<1, 1, 0, st>>>(m, kind, k, dot_dev, lv.lcost.p, avg, lt.as<int32_t>());
+        k_level_targets<<<1, 1, 0, st>>>(m, kind, k, dot_dev, lv.lcost.p, avg, (int)std::max<int64_t>(1, parts),
+                                          lt.as<int32_t>());
         k_map_targets<<<nblk(n, 256), 256, 0, st>>>(n, lv.level.p, lt.as<int32_t>(), target);
         SP_CUDA(cudaGetLastError());
         return SPTRSV_OK;
     }
-    Scratch rc, doff, dlen, eoff, elen, info, status;
+    parts = (int)std::max<int64_t>(1, std::min<int64_t>(parts, std::max<int64_t>(1, m)));
+    Scratch rc, doff, dlen, eoff, elen, info, status, plim;
     SP_TRY(rc.alloc(n * 8, st));
     SP_TRY(doff.alloc(n * 8, st));
     SP_TRY(dlen.alloc(n * 4, st));
     SP_TRY(eoff.alloc(n * 8, st));
     SP_TRY(elen.alloc(n * 4, st));
-    SP_TRY(info.alloc(4 * 8, st));
+    SP_TRY(info.alloc((size_t)parts * 3 * 8, st));
     SP_TRY(status.alloc(sizeof(int), st));
-    int64_t cap_pool = std::max<int64_t>(1 << 22, (cap > 0 ? 2 : 16) * L->nnz);
+    SP_TRY(plim.alloc((size_t)parts * 8, st));
+    // the nnz cap's allowance, shared by the level ranges in proportion to their entries
+    std::vector<int64_t> h_plim(parts, INT64_MAX);
+    if (cap > 0) {
+        const int64_t allowance = (int64_t)std::floor(cap * (double)L->nnz) - L->nnz;
+        std::vector<int64_t> h_lnnz(std::max<int64_t>(1, m));
+        SP_CUDA(cudaMemcpyAsync(h_lnnz.data(), lv.lnnz.p, m * 8, cudaMemcpyDeviceToHost, st));
+        SP_CUDA(cudaStreamSynchronize(st));
+        for (int w = 0; w < parts; ++w) {
+            int64_t z = 0;
+            for (int64_t l = m * w / parts; l < m * (w + 1) / parts; ++l) z += h_lnnz[l];
+            h_plim[w] = L->nnz > 0 ? allowance * z / L->nnz : 0;
+        }
+    }
+    SP_CUDA(cudaMemcpyAsync(plim.p, h_plim.data(), (size_t)parts * 8, cudaMemcpyHostToDevice, st));
+    int64_t cap_pool = std::max<int64_t>(1 << 20, (cap > 0 ? 2 : 16) * L->nnz / parts * (parts > 1 ? 2 : 1));
     for (int attempt = 0; attempt < 6; ++attempt) {
         Scratch pool;
-        SP_TRY(pool.alloc((size_t)cap_pool * sizeof(int32_t), st));
+        SP_TRY(pool.alloc((size_t)cap_pool * parts * sizeof(int32_t), st));
         SP_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st));
         k_init_walk<<<nblk(n, 256), 256, 0, st>>>(n, L->rowptr, lv.level.p, target, rc.as<int64_t>());
         WalkArgs a;
@@ -535,7 +565,7 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
         a.kind = kind;
         a.k = k;
         a.avg = avg;
-        a.limit = cap > 0 ? (int64_t)std::floor(cap * (double)L->nnz) : INT64_MAX;
+        a.part_limit = plim.as<int64_t>();
         a.dot = dot_dev;
         a.inj = inj;
         a.alpha = alpha;
@@ -550,21 +580,26 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
         a.pool_cap = cap_pool;
         a.info = info.as<int64_t>();
         a.status = status.as<int>();
-        k_plan_walk<<<1, 32, 0, st>>>(a);
+        k_plan_walk<<<parts, 32, 0, st>>>(a);
         SP_CUDA(cudaGetLastError());
         int hs = 0;
-        int64_t hi[3];
+        std::vector<int64_t> hi((size_t)parts * 3);
         SP_CUDA(cudaMemcpyAsync(&hs, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        SP_CUDA(cudaMemcpyAsync(hi, info.p, 3 * 8, cudaMemcpyDeviceToHost, st));
+        SP_CUDA(cudaMemcpyAsync(hi.data(), info.p, (size_t)parts * 3 * 8, cudaMemcpyDeviceToHost, st));
         SP_CUDA(cudaStreamSynchronize(st));
         if (hs == DEV_OVERFLOW) {
             cap_pool *= 4;
             continue;
         }
         if (hs != 0) return map_dev_status(hs, "rewrite: planner");
-        po.moved = hi[0];
-        po.stored = hi[1];
-        po.targets = hi[2];
+        po.moved = 0;
+        po.stored = L->nnz;
+        po.targets = 0;
+        for (int w = 0; w < parts; ++w) {
+            po.moved += hi[3 * w];
+            po.stored += hi[3 * w + 1];
+            po.targets += hi[3 * w + 2];
+        }
         return SPTRSV_OK;
     }
     set_error("rewrite: planner scratch exceeded %lld entries", (long long)cap_pool);
@@ -703,7 +738,7 @@ sptrsv_status rewrite_rows(const sptrsv_csr* L, const Levels& lv, const int32_t*
 
 sptrsv_status rewrite_system(const sptrsv_csr* L, const Levels& lv, int kind, int k, const int32_t* dot_dev,
                              double avg_override, double cap, double guard, const int64_t* inj, int alpha, int64_t beta,
-                             sptrsv_system** out, cudaStream_t st) {
+                             int parts, sptrsv_system** out, cudaStream_t st) {
     const int64_t n = L->n;
     sptrsv_system* s = new (std::nothrow) sptrsv_system();
     if (!s) { set_error("host allocation failed"); return SPTRSV_ERR_OOM; }
@@ -721,7 +756,7 @@ sptrsv_status rewrite_system(const sptrsv_csr* L, const Levels& lv, int kind, in
     if (rc != SPTRSV_OK) return fail(rc);
     PlanOut po;
     if (n > 0) {
-        rc = plan_targets(L, lv, kind, k, dot_dev, avg, cap, inj, alpha, beta, s->target.p, po, st);
+        rc = plan_targets(L, lv, kind, k, dot_dev, avg, cap, inj, alpha, beta, parts, s->target.p, po, st);
         if (rc != SPTRSV_OK) return fail(rc);
         rc = L->dtype == SPTRSV_F64 ? rewrite_rows<double>(L, lv, s->target.p, guard, s, st)
                                     : rewrite_rows<float>(L, lv, s->target.p, guard, s, st);
@@ -781,7 +816,8 @@ extern "C" sptrsv_status sptrsv_rewrite(const sptrsv_csr* L, const sptrsv_levels
     if (!wk) { set_error("rewrite: unknown strategy %d", kind); return SPTRSV_ERR_INVALID; }
     const int k = kind == SPTRSV_STRATEGY_ROWCAP && sg->k <= 0 ? ROWCAP_DEFAULT_ROWS : sg->k;
     sptrsv_status rc = rewrite_system(L, lv, wk, k, dot_dev, sg->avg_override, sg->nnz_growth_cap,
-                                      sg->growth_guard, sg->injected_cost_dev, sg->max_deps, sg->max_spread, out, st);
+                                      sg->growth_guard, sg->injected_cost_dev, sg->max_deps, sg->max_spread,
+                                      sg->walk_parts, out, st);
     if (rc == SPTRSV_OK) (*out)->strategy_used = kind;
     return rc;
 }

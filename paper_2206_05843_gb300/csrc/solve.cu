@@ -70,8 +70,8 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     }
     if (a.nseg == 0) return SPTRSV_OK;
     if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
-    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize, sc.tile_ecap));  // systems may differ in their shared memory
-    SP_CUDA(launch_k_solve<T>(a, sc.grid, sc.block, sc.smem, sc.csize, st));
+    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize, sc.tile_ecap, sc.runs));  // systems may differ in their shared memory
+    SP_CUDA(launch_k_solve<T>(a, sc.grid, sc.block, sc.smem, sc.csize, st, sc.runs));
     return SPTRSV_OK;
 }
 
@@ -414,7 +414,10 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     sc.ring_rows = ring_rows;
     sc.stage_rows = stage_rows;
     sc.stage_entries = stage_entries;
+    sc.runs = 0;
+    for (const int4& sg : sc.h_segs) sc.runs += (sg.x & SEG_TYPE_MASK) == SEG_RUN;
     sc.smem = sc.tile_ecap > 0 ? std::max(smem, 2 * tile_buf_bytes(sc.tile_ecap, vb)) : smem;
+    if (csize == 1 && sc.tile_ecap == 0 && sc.runs == 0) sc.smem = 0;  // wide levels only: no staging
     SP_TRY(s->flags.ensure((size_t)std::max(1, sc.grid)));
     SP_TRY(s->status.ensure(1));
     return SPTRSV_OK;

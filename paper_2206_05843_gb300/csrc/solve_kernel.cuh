@@ -211,6 +211,111 @@ __device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, 
     return true;
 }
 
+// Wide level, one right-hand side, one lane per row, in the kernel variant for schedules without
+// single-CTA runs (registers to spare): as wide_rows_1rhs for the first row; after it, a row's
+// coefficients are loaded eight at a time (their gathers in flight together), and the next row's
+// position data (perm, row pointers, 1 / L_rr) one row ahead, so that a row costs one round trip
+// to memory less.
+template <typename T>
+__device__ __forceinline__ T row_1rhs8(const SolveArgs<T>& a, int c0, int c1, T acc) {
+    for (int q = c0; q < c1; q += 8) {
+        int cc[8];
+        T cv[8], xv[8];
+        if ((q & 3) == 0 && q + 8 <= c1) {
+            const int4 i0 = __ldcs((const int4*)(a.ccol + q)), i1 = __ldcs((const int4*)(a.ccol + q + 4));
+            cc[0] = i0.x; cc[1] = i0.y; cc[2] = i0.z; cc[3] = i0.w;
+            cc[4] = i1.x; cc[5] = i1.y; cc[6] = i1.z; cc[7] = i1.w;
+            if (sizeof(T) == 8) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const double2 v = __ldcs((const double2*)(a.cval + q) + h);
+                    cv[2 * h] = (T)v.x;
+                    cv[2 * h + 1] = (T)v.y;
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float4 v = __ldcs((const float4*)(a.cval + q) + h);
+                    cv[4 * h] = (T)v.x; cv[4 * h + 1] = (T)v.y; cv[4 * h + 2] = (T)v.z; cv[4 * h + 3] = (T)v.w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool ok = q + u < c1;
+                cc[u] = ok ? __ldcs(a.ccol + q + u) : 0;
+                cv[u] = ok ? __ldcs(a.cval + q + u) : T(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = q + u < c1 ? __ldcg(a.xp + cc[u]) : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (q + u < c1) acc -= cv[u] * xv[u];
+    }
+    return acc;
+}
+
+template <typename T, typename WaitFn>
+__device__ bool wide_rows_1rhs_ilp(const SolveArgs<T>& a, int64_t my0, int64_t my1, WaitFn wait) {
+    const int64_t pf = my0 + threadIdx.x;
+    const bool act0 = pf < my1;
+    const int32_t row0 = act0 ? __ldcs(a.perm + pf) : 0;
+    const int f0 = act0 ? __ldcs(a.cptr + pf) : 0, f1 = act0 ? __ldcs(a.cptr + pf + 1) : 0;
+    T pre = act0 ? __ldcs(a.dinv + pf) * __ldcs(a.b + row0) : T(0);
+    int32_t pcol[PF];
+    T pval[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+        const bool ok = f0 + u < f1;
+        pcol[u] = ok ? __ldcs(a.ccol + f0 + u) : 0;
+        pval[u] = ok ? __ldcs(a.cval + f0 + u) : T(0);
+    }
+    // the second row's position data, independent of x
+    int64_t p = pf + blockDim.x;
+    bool actn = p < my1;
+    int32_t rown = actn ? __ldcs(a.perm + p) : 0;
+    int c0n = actn ? __ldcs(a.cptr + p) : 0, c1n = actn ? __ldcs(a.cptr + p + 1) : 0;
+    T din = actn ? __ldcs(a.dinv + p) : T(0);
+    if (!wait()) return false;
+    if (act0) {
+        T xv[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) xv[u] = f0 + u < f1 ? __ldcg(a.xp + pcol[u]) : T(0);
+        T acc = pre;
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (f0 + u < f1) acc -= pval[u] * xv[u];
+        acc = row_1rhs(a, pf, row0, f0 + PF < f1 ? f0 + PF : f1, f1, acc);
+        __stcg(a.xp + pf, acc);
+        a.x[row0] = acc;
+    }
+    while (actn) {
+        const int32_t row = rown;
+        const int c0 = c0n, c1 = c1n;
+        const T di = din;
+        const T bv = __ldcs(a.b + row);
+        const int64_t pn = p + blockDim.x;
+        actn = pn < my1;
+        if (actn) {
+            rown = __ldcs(a.perm + pn);
+            c0n = __ldcs(a.cptr + pn);
+            c1n = __ldcs(a.cptr + pn + 1);
+            din = __ldcs(a.dinv + pn);
+        }
+        T acc = di * bv;
+        if (a.eptr) {
+            const int e1 = __ldcs(a.eptr + p + 1);
+            for (int q = __ldcs(a.eptr + p); q < e1; ++q) acc += __ldcs(a.eval + q) * a.b[__ldcs(a.ecol + q)];
+        }
+        acc = row_1rhs8(a, c0, c1, acc);
+        __stcg(a.xp + p, acc);
+        __stcs(a.x + row, acc);
+        p = pn;
+    }
+    return true;
+}
+
 // One level per launch (the plain level-set solve): every row of the level is a thread,
 // so the whole level is in flight at full occupancy.  Used when the schedule consists of
 // a few wide levels, where one launch per level costs less than a device-wide handoff
@@ -438,13 +543,15 @@ __device__ __forceinline__ bool level_rows(const SolveArgs<T>& a, const Lanes& l
 // flag waits, and publishes nothing, so that the CTAs waiting on it run out too; inside a cluster
 // region it still takes every cluster barrier, so that no CTA of its cluster waits on it forever.
 // No CTA returns early.
-// kernel variants (one register allocation each): plain, plain with tiled WIDE levels, cluster
-enum KMode : int { KM_PLAIN = 0, KM_TILED = 1, KM_CLUSTER = 2 };
+// kernel variants (one register allocation each): plain, plain with tiled WIDE levels, cluster, and
+// WIDE levels only (no single-CTA runs, no shared memory)
+enum KMode : int { KM_PLAIN = 0, KM_TILED = 1, KM_CLUSTER = 2, KM_WIDE = 3 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
+__global__ void __launch_bounds__(512, MODE == 2 ? 1 : 2) k_solve(SolveArgs<T> a) {
     constexpr bool CL = MODE == KM_CLUSTER;
     constexpr bool TL = MODE == KM_TILED;
+    constexpr bool WO = MODE == KM_WIDE;
     unsigned char* smem = g_dyn_smem;
     const int nrhs = a.nrhs;
     const Lanes ln = make_lanes(a.lpr, nrhs);
@@ -475,6 +582,9 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
                     ok = (sg.x & SEG_TILED)
                              ? wide_rows_tiled(a, my0, my1, TILE_ROWS >> ((sg.x >> SEG_TILE_SHIFT) & 3), tc, w)
                              : level_rows(a, ln, wl, my0, my1, w);
+                } else if constexpr (WO) {
+                    ok = (nrhs == 1 && (wl == 1 || (wl == 0 && a.lpr == 1))) ? wide_rows_1rhs_ilp(a, my0, my1, w)
+                                                                             : level_rows(a, ln, wl, my0, my1, w);
                 } else {
                     ok = level_rows(a, ln, wl, my0, my1, w);
                 }
@@ -482,7 +592,7 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
                 publish(a, s);
                 if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
             } else {
-                if (me != 0) continue;
+                if (WO || me != 0) continue;  // the wide-only variant never holds a run
                 SysView<T> v{nrhs,   a.ld,   a.perm, a.lptr, a.cptr, a.ccol, a.cval,
                              a.dinv, a.eptr, a.ecol, a.eval, a.b,    a.x,    a.xp,
                              a.pre ? a.xp : nullptr};
@@ -559,17 +669,23 @@ __global__ void __launch_bounds__(512, 2) k_solve(SolveArgs<T> a) {
 // Kernel attributes of the k_solve instantiation a launch with csize CTAs per cluster uses
 // the variant a schedule runs: cluster when it has CLUSTER segments, tiled when it has tiled WIDE
 // segments, else plain
-inline int k_mode(int csize, int tile_ecap) { return csize > 1 ? KM_CLUSTER : (tile_ecap > 0 ? KM_TILED : KM_PLAIN); }
-
-template <typename T>
-const void* k_solve_fn(int mode) {
-    return mode == KM_CLUSTER ? (const void*)k_solve<T, KM_CLUSTER>
-                              : (mode == KM_TILED ? (const void*)k_solve<T, KM_TILED> : (const void*)k_solve<T, KM_PLAIN>);
+inline int k_mode(int csize, int tile_ecap, int runs = 1) {
+    return csize > 1 ? KM_CLUSTER : (tile_ecap > 0 ? KM_TILED : (runs == 0 ? KM_WIDE : KM_PLAIN));
 }
 
 template <typename T>
-cudaError_t k_solve_attrs(size_t smem, int csize, int tile_ecap) {
-    const void* fn = k_solve_fn<T>(k_mode(csize, tile_ecap));
+const void* k_solve_fn(int mode) {
+    switch (mode) {
+        case KM_CLUSTER: return (const void*)k_solve<T, KM_CLUSTER>;
+        case KM_TILED: return (const void*)k_solve<T, KM_TILED>;
+        case KM_WIDE: return (const void*)k_solve<T, KM_WIDE>;
+        default: return (const void*)k_solve<T, KM_PLAIN>;
+    }
+}
+
+template <typename T>
+cudaError_t k_solve_attrs(size_t smem, int csize, int tile_ecap, int runs = 1) {
+    const void* fn = k_solve_fn<T>(k_mode(csize, tile_ecap, runs));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && csize > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
@@ -578,8 +694,9 @@ cudaError_t k_solve_attrs(size_t smem, int csize, int tile_ecap) {
 // Launches k_solve for a prepared schedule: cooperative (all CTAs co-resident, so every bounded
 // wait can succeed), and with the schedule's cluster size when it has CLUSTER segments.
 template <typename T>
-cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t smem, int csize, cudaStream_t st) {
-    const int mode = k_mode(csize, a.tile_ecap);
+cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t smem, int csize, cudaStream_t st,
+                           int runs = 1) {
+    const int mode = k_mode(csize, a.tile_ecap, runs);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
@@ -600,6 +717,7 @@ cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t sm
     cfg.numAttrs = na;
     if (mode == KM_CLUSTER) return cudaLaunchKernelEx(&cfg, k_solve<T, KM_CLUSTER>, a);
     if (mode == KM_TILED) return cudaLaunchKernelEx(&cfg, k_solve<T, KM_TILED>, a);
+    if (mode == KM_WIDE) return cudaLaunchKernelEx(&cfg, k_solve<T, KM_WIDE>, a);
     return cudaLaunchKernelEx(&cfg, k_solve<T, KM_PLAIN>, a);
 }
 

@@ -101,11 +101,11 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
         SP_CUDA(cudaGetLastError());
         return SPTRSV_OK;
     }
-    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize, sc.tile_ecap));
+    SP_CUDA(k_solve_attrs<T>(sc.smem, sc.csize, sc.tile_ecap, sc.runs));
     SP_CUDA(cudaMemsetAsync(a.flags, 0xff, (size_t)sc.grid * sizeof(int), st));
     if (a.nseg == 0) return SPTRSV_OK;
     if (sc.pre) k_bparts<T><<<sc.pre_grid, 256, 0, st>>>(a, (int)sc.h_blocks.size());
-    SP_CUDA(launch_k_solve<T>(a, sc.grid, sc.block, sc.smem, sc.csize, st));
+    SP_CUDA(launch_k_solve<T>(a, sc.grid, sc.block, sc.smem, sc.csize, st, sc.runs));
     return SPTRSV_OK;
 }
 

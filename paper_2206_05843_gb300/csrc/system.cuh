@@ -58,6 +58,7 @@ struct Schedule {
     int stage_rows = 0, stage_entries = 0;
     int pre = 0;       // a b-part kernel runs before the solve (rewritten rows in staged blocks)
     int tile_ecap = 0; // coefficients a tile buffer holds (0: no tiled WIDE segments)
+    int runs = 0;      // RUN segments (0: the wide-only kernel variant, no shared memory)
     int64_t tiled_levels = 0;
     int pre_grid = 0;  // its CTAs
     size_t smem = 0;
@@ -152,7 +153,7 @@ sptrsv_status pack_system(sptrsv_system* s, const sptrsv_csr* L, const RewriteHe
 // rewrite with a planner walk kind (1 naive, 2 fixed depth, 3 depth per target) -> new system
 sptrsv_status rewrite_system(const sptrsv_csr* L, const Levels& lv, int kind, int k, const int32_t* dot_dev,
                              double avg_override, double cap, double guard, const int64_t* inj, int alpha, int64_t beta,
-                             sptrsv_system** out, cudaStream_t st);
+                             int parts, sptrsv_system** out, cudaStream_t st);
 
 // median time of `reps` solves with b = 0 (one right-hand side), in microseconds
 sptrsv_status time_solve_us(sptrsv_system* s, int reps, double* us, cudaStream_t st);

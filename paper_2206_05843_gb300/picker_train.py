@@ -73,7 +73,7 @@ def candidate_depths(rows: np.ndarray, c: int) -> np.ndarray:
     return np.maximum(j - 1 - np.arange(m), 0).astype(np.int32)
 
 
-def harvest(m, depths=DEPTHS, reps=3, seed=0, per_candidate=20000):
+def harvest(m, depths=DEPTHS, reps=3, seed=0, per_candidate=2000):
     """Samples (features, dt in ns) of one matrix: every target of a thin-level plan with the
     candidate's depths (no nnz cap, so that every group holds its whole window); at most
     per_candidate targets per candidate, drawn at random."""
@@ -170,7 +170,7 @@ def solve_time_us(sysm, bt, reps=5):
     return statistics.median(ts), x
 
 
-def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
+def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9, walk_parts=1):
     """Solve time of no rewrite, the paper's naive strategy, the ROWCAP plan and the network's own
     plan (the learned strategy with model_only), each with its error against x_true (b = L x_true).
     The learned strategy's measured choice is the fastest of those four (the library times the
@@ -191,9 +191,10 @@ def evaluate(pk, mats, cap=1.5, log=None, time_budget=1e9):
         bt = torch.from_numpy(b[0]).cuda()
         ref = xt[0]
         res = {"n": m.n, "levels": lv.m}
-        for name, kw in (("none", {}), ("naive", dict(kind=B.NAIVE, cap=cap)),
-                         ("rowcap", dict(kind=B.ROWCAP, k=32, cap=cap)),
-                         ("learned_model_only", dict(kind=B.LEARNED, cap=cap, picker=pk, model_only=True))):
+        wp = dict(walk_parts=walk_parts)
+        for name, kw in (("none", {}), ("naive", dict(kind=B.NAIVE, cap=cap, **wp)),
+                         ("rowcap", dict(kind=B.ROWCAP, k=32, cap=cap, **wp)),
+                         ("learned_model_only", dict(kind=B.LEARNED, cap=cap, picker=pk, model_only=True, **wp))):
             s = B.System(M, lv, **kw)
             us, x = solve_time_us(s, bt)
             err = float(np.linalg.norm(x.cpu().numpy() - ref) / np.linalg.norm(ref))
@@ -241,6 +242,9 @@ def main(argv=None):
     ap.add_argument("--evaluate", default=None, help="evaluate this trained picker file only (no training)")
     ap.add_argument("--save-data", default=None, help="write the harvested samples to this .npz file")
     ap.add_argument("--load-data", default=None, help="train on samples from this .npz file (no harvest)")
+    ap.add_argument("--walk-parts", type=int, default=1, help="level ranges the evaluation's planner walks start at")
+    ap.add_argument("--per-candidate", type=int, default=2000, help="targets sampled per candidate and matrix")
+    ap.add_argument("--also-evaluate", default=None, help="evaluate this second picker file on the same matrices")
     a = ap.parse_args(argv)
 
     def log(s):
@@ -253,7 +257,7 @@ def main(argv=None):
         for i in range(a.heldout):
             n = int(round(np.exp(erng.uniform(np.log(a.eval_lo), np.log(a.eval_hi)))))
             mats.append(lambda n=n, i=i: S.gen_mixture(n, 20_000 + i))
-        rows, summary = evaluate(pk, mats, log=log, time_budget=a.eval_budget)
+        rows, summary = evaluate(pk, mats, log=log, time_budget=a.eval_budget, walk_parts=a.walk_parts)
         json.dump({"picker": a.evaluate, "summary": summary, "heldout": rows}, open(a.report, "w"), indent=1)
         log(json.dumps(summary))
         return 0
@@ -270,7 +274,7 @@ def main(argv=None):
                 break
             n = int(round(np.exp(rng.uniform(np.log(a.n_lo), np.log(a.n_hi)))))
             m = S.gen_mixture(n, 10_000 + i)
-            X, Y = harvest(m, seed=i)
+            X, Y = harvest(m, seed=i, per_candidate=a.per_candidate)
             Xs.append(X)
             Ys.append(Y)
             used += 1
@@ -288,10 +292,15 @@ def main(argv=None):
     for i in range(a.heldout):
         n = int(round(np.exp(erng.uniform(np.log(a.eval_lo), np.log(a.eval_hi)))))
         mats.append(lambda n=n, i=i: S.gen_mixture(n, 20_000 + i))
-    rows, summary = evaluate(pk, mats, log=log, time_budget=a.eval_budget)
+    rows, summary = evaluate(pk, mats, log=log, time_budget=a.eval_budget, walk_parts=a.walk_parts)
     report = {"train_matrices": used, "heldout_requested": a.heldout, "samples": int(X.shape[0]),
               "loss_history": hist, "summary": summary,
-              "heldout": rows, "depths": DEPTHS}
+              "heldout": rows, "depths": DEPTHS, "walk_parts": a.walk_parts}
+    if a.also_evaluate:
+        mats2 = mats[:len(rows)]
+        rows2, summary2 = evaluate(B.Picker.load(a.also_evaluate), mats2, log=log, walk_parts=a.walk_parts)
+        report["also_evaluated"] = {"picker": a.also_evaluate, "summary": summary2}
+        log(json.dumps(summary2))
     json.dump(report, open(a.report, "w"), indent=1)
     log(json.dumps(summary))
     return 0

@@ -18,13 +18,13 @@ KIND = {B.NAIVE: O.NAIVE, B.DEPTH_K: O.DEPTH, B.CHOSEN: O.CHOSEN, B.MANUAL: O.MA
         B.CHOSEN_THIN: O.CHOSEN_THIN}
 
 
-def run_both(m, kind, b=None, k=0, cap=0.0, depth_of_target=None, exact=True):
+def run_both(m, kind, b=None, k=0, cap=0.0, depth_of_target=None, exact=True, parts=1):
     torch = torch_cuda()
     M = B.Matrix.from_host(m)
     lv = B.Levels(M)
     lev, mm = O.levels(m.rowptr, m.colidx)
-    p = O.plan(m.rowptr, m.colidx, lev, mm, KIND[kind], k=k, cap=cap, depth_of_target=depth_of_target)
-    sysm = B.System(M, lv, kind, k=k, cap=cap, depth_of_target=depth_of_target)
+    p = O.plan(m.rowptr, m.colidx, lev, mm, KIND[kind], k=k, cap=cap, depth_of_target=depth_of_target, parts=parts)
+    sysm = B.System(M, lv, kind, k=k, cap=cap, depth_of_target=depth_of_target, walk_parts=parts)
     ex = sysm.export()
     # the plan
     assert np.array_equal(ex["target"], p.target)
@@ -225,3 +225,19 @@ def test_manual_without_cap_maps_levels():
     _, b = S.rhs_from_xtrue(m, 1, 4)
     for k in (2, 9):
         run_both(m, B.MANUAL, b, k=k)
+
+
+@pytest.mark.parametrize("parts", [2, 7, 64])
+@pytest.mark.parametrize("kind,k", [(B.NAIVE, 0), (B.ROWCAP, 32), (B.MANUAL, 9), (B.DEPTH_K, 3)])
+def test_walk_started_at_several_places(kind, k, parts):
+    """The planner walk started at the beginning of every level range (one warp per range at the same
+    time; 2 ranges: from both ends), with and without the nnz cap: plans identical to the oracle's."""
+    m = S.gen_mixture(60_000, 10_777)
+    _, b = S.rhs_from_xtrue(m, 1, 6)
+    for cap in (0.0, 1.5):
+        run_both(m, kind, b, k=k, cap=cap, parts=parts)
+
+
+def test_walk_parts_full_size_skewed():
+    m, b, _ = S.gen_config("c1")
+    run_both(m, B.ROWCAP, b, k=32, cap=1.5, parts=64)

@@ -203,3 +203,17 @@ def test_per_level_launch_mode(nrhs):
     solve_and_compare(m, b, TOL_F64, tune=dict(run_width=-2))
     m2, b2, _ = S.gen_config("c0")
     solve_and_compare(m2, b2, TOL_F64, system_kw=dict(kind=B.NAIVE, cap=1.5), tune=dict(run_width=-2))
+
+
+@pytest.mark.parametrize("k", [3, 5, 8, 11, 17])
+def test_wide_only_schedules(k):
+    """Schedules of wide levels only (no single-CTA runs) run the kernel variant without shared
+    memory, whose rows load their coefficients eight at a time: rows of 3..17 coefficients
+    (aligned and unaligned, shorter and longer than eight), plain and after a depth-1 rewrite
+    (rewritten rows with E entries in wide levels)."""
+    m = S.gen_layered(6, 30_000, 21, k=k)
+    _, b = S.rhs_from_xtrue(m, 1, 3)
+    for kw in ({}, dict(kind=B.DEPTH_K, k=1)):
+        s, x, ref = solve_and_compare(m, b, TOL_F64, system_kw=kw, tune=dict(lanes_per_row=1))
+        info = s.refresh()
+        assert info["run_levels"] == 0 and info["cluster_levels"] == 0

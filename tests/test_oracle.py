@@ -536,3 +536,69 @@ def test_planner_naive_rewritten_row_cost_hand_derived(name):
     for r, d in case["deps_after"].items():
         assert int(sy.cptr[r + 1] - sy.cptr[r]) == d
         assert p.row_cost[r] == 2 * d
+
+
+# ---------------------------------------------------------------------------------
+# the walk started at several places (Section III: also from the end of the graph)
+# ---------------------------------------------------------------------------------
+
+def _chain(n, seed=0):
+    return S.gen_from_deps(n, np.array([0] + [1] * (n - 1)), np.arange(n - 1), S.rng_for(seed))
+
+
+def test_planner_parts_depth_chain_hand_derived():
+    """DEPTH k = 2 on a chain of 10 one-row levels.  One walk: targets every third level.  With
+    P ranges every range [w*10/P, (w+1)*10/P) starts its own groups of three."""
+    m = _chain(10)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    want = {1: [0, 0, 0, 3, 3, 3, 6, 6, 6, 9],
+            2: [0, 0, 0, 3, 3, 5, 5, 5, 8, 8],       # ranges [0,5), [5,10)
+            3: [0, 0, 0, 3, 3, 3, 6, 6, 6, 9],       # ranges [0,3), [3,6), [6,10): the same as one walk
+            4: [0, 0, 2, 2, 2, 5, 5, 7, 7, 7]}       # ranges [0,2), [2,5), [5,7), [7,10)
+    for parts, tgt in want.items():
+        p = O.plan(m.rowptr, m.colidx, lev, mm, O.DEPTH, k=2, parts=parts)
+        assert p.target.tolist() == tgt, parts
+    # more ranges than levels: every level starts a range, nothing moves
+    p = O.plan(m.rowptr, m.colidx, lev, mm, O.DEPTH, k=2, parts=25)
+    assert p.target.tolist() == list(range(10)) and p.moved == 0
+
+
+def test_planner_parts_cap_share_hand_derived():
+    """DEPTH k = 8 on a chain of 9 one-row levels with the nnz cap 2.0: nnz(L) = 17, allowance 17.
+    Moving row i into level 0 adds i entries (its E row grows by one substitution per row above).
+    One walk takes rows 1..5 (15), rejects row 6 (21 > 17): level 6 is a target; row 7 joins it
+    (+2, 17), row 8 does not (+3): level 8 is a target.  Two ranges, levels [0,4) with 7 entries and
+    [4,9) with 10: shares 17*7/17 = 7 and 17*10/17 = 10; range 0 moves rows 1..3 (1+2+3 = 6); range 1
+    starts a target at 4 and moves rows 5, 6, 7 (+2, +3, +4 = 9) but not 8 (+5 > 10)."""
+    m = _chain(9)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    p1 = O.plan(m.rowptr, m.colidx, lev, mm, O.DEPTH, k=8, cap=2.0)
+    assert p1.target.tolist() == [0, 0, 0, 0, 0, 0, 6, 6, 8]
+    assert p1.stored_nnz == 17 + 15 + 2
+    p2 = O.plan(m.rowptr, m.colidx, lev, mm, O.DEPTH, k=8, cap=2.0, parts=2)
+    assert p2.target.tolist() == [0, 0, 0, 0, 4, 4, 4, 4, 8]
+    assert p2.stored_nnz == 17 + 6 + 9
+
+
+@pytest.mark.parametrize("kind,k", [(O.NAIVE, 0), (O.ROWCAP, 32), (O.MANUAL, 9), (O.DEPTH, 3)])
+@pytest.mark.parametrize("parts", [2, 5])
+def test_planner_parts_invariants(kind, k, parts):
+    """Rows never move across a range start; the first eligible level of every range keeps its rows;
+    the rewrite of the plan is still the elimination E L, and with the cap each range stays within
+    its share."""
+    m = S.gen_mixture(6000, 10_555)
+    lev, mm = O.levels(m.rowptr, m.colidx)
+    for cap in (0.0, 1.3):
+        p = O.plan(m.rowptr, m.colidx, lev, mm, kind, k=k, cap=cap, parts=parts)
+        starts = [mm * w // parts for w in range(parts)]
+        rng_of = np.searchsorted(starts, lev, side="right") - 1
+        assert np.all(p.target >= np.array(starts)[rng_of])
+        for s0 in starts:
+            assert np.all(p.target[lev == s0] == s0)
+        if cap:
+            assert p.stored_nnz <= math.floor(cap * p.nnz_l)
+        sy = O.rewrite(m.rowptr, m.colidx, m.vals, lev, p.target)
+        stored = int(sy.cptr[-1]) + m.n + int(sy.eptr[-1])
+        assert stored == p.stored_nnz
+        b = S.rhs_uniform(m.n, 1, 2)[0]
+        assert np.allclose(sy.solve(b), O.forward_subst(m.rowptr, m.colidx, m.vals, b), rtol=1e-9, atol=1e-12)
