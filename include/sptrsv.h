@@ -123,7 +123,7 @@ enum {
                                     chooses per target (NAIVE without a picker) */
     SPTRSV_STRATEGY_CHOSEN = 4,  /* depth per target given by the caller */
     SPTRSV_STRATEGY_MANUAL = 5,  /* fixed distance k over thin levels only: the manual approach of the earlier work
-                                    ("every 9 levels into the 10th", Sections III and IV) */
+                                    (nine levels folded into each tenth, Sections III and IV) */
     SPTRSV_STRATEGY_ROWCAP = 6,  /* the Section III walk over thin levels with a row count in place of avgLevelCost:
                                     a target takes rows while it holds at most k of them (k <= 0: 32, one warp's
                                     lanes -- the width of a level in the fast thin-level executor) */

@@ -174,7 +174,7 @@ static void iset_free(iset* s) { free(s->v); s->v = NULL; s->len = s->cap = 0; }
 #define ORC_NAIVE 1   /* avgLevelCost over thin levels */
 #define ORC_DEPTH 2   /* fixed distance: target every (k+1)-th level, k levels merged in */
 #define ORC_CHOSEN 3  /* per-target depth given by the caller (learned picker) */
-#define ORC_MANUAL 4  /* fixed distance over thin levels only: "every 9 levels into the 10th"
+#define ORC_MANUAL 4  /* fixed distance over thin levels only: nine levels folded into each tenth,
                          applied to the levels cheaper than avgLevelCost (Section IV) */
 #define ORC_CHOSEN_THIN 5  /* per-target depth over thin levels only: the learned picker's
                               depth choice within the thin-level rule of Section III */

@@ -52,6 +52,7 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     a.stage_rows = sc.stage_rows;
     a.stage_entries = sc.stage_entries;
     a.pre = sc.pre;
+    a.pre_cl = sc.pre_cl;
     a.csize = sc.csize;
     a.tile_ecap = sc.tile_ecap;
 
@@ -393,7 +394,22 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     }
     // rewritten rows in thin levels: their b-parts (E rows) are computed up front by every
     // CTA, so that staging reads one value per row instead of walking the E row
-    sc.pre = s->nnz_e > 0 && !sc.h_blocks.empty() && nrhs * (int64_t)vb <= 64 ? 1 : 0;
+    const bool small_rhs = nrhs * (int64_t)vb <= 64;
+    const bool run_pre = s->nnz_e > 0 && !sc.h_blocks.empty();
+    // the rows of CLUSTER segments too: a cluster row then reads one contiguous b-part instead of
+    // gathering b through the permutation after the level's wait (ranges of at most 4,096 positions,
+    // after the run blocks, so that the runs' block indices stay as they are)
+    sc.pre_cl = 0;
+    if (csize > 1 && small_rhs) {
+        for (const int4& sg : sc.h_segs) {
+            if ((sg.x & SEG_TYPE_MASK) != SEG_CLUSTER) continue;
+            for (int64_t q = lp[sg.y]; q < lp[sg.z]; q += 4096) {
+                sc.h_blocks.push_back(make_int4((int)q, (int)std::min<int64_t>(lp[sg.z], q + 4096), 0, 0));
+                sc.pre_cl = 1;
+            }
+        }
+    }
+    sc.pre = small_rhs && (run_pre || sc.pre_cl) ? 1 : 0;
     sc.pre_grid = (int)std::min<int64_t>((int64_t)sc.h_blocks.size(), (int64_t)sms * 8);
     if (sc.h_blocks.empty()) sc.h_blocks.push_back(make_int4(0, 0, 0, 0));
     SP_TRY(sc.segs.alloc(std::max<size_t>(1, sc.h_segs.size())));

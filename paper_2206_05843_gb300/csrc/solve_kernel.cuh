@@ -66,7 +66,8 @@ __device__ __forceinline__ T bpart(const SolveArgs<T>& a, int64_t p, int32_t row
 
 // Wide level, several right-hand sides or several lanes per row: the first row of each
 // thread is prepared (coefficients in registers, b-part) before the wait.
-template <typename T, typename WaitFn>
+// PRE: the b-parts of these rows were computed before the solve (k_bparts) and sit in xp
+template <typename T, typename WaitFn, bool PRE = false>
 __device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ngroups, int grp, int64_t my0,
                                   int64_t my1, WaitFn wait) {
     const int nrhs = a.nrhs;
@@ -85,7 +86,8 @@ __device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ng
         pcol[u] = ok ? a.ccol[q] : -1;
         pval[u] = ok ? a.cval[q] : T(0);
     }
-    if (act0 && single && ln.rl < nrhs) pre = bpart(a, pf, row0, ln.rl, ln);
+    if (act0 && single && ln.rl < nrhs)
+        pre = PRE ? (ln.el == 0 ? __ldcg(a.xp + pf * nrhs + ln.rl) : T(0)) : bpart(a, pf, row0, ln.rl, ln);
     if (!wait()) return false;
     for (int64_t base = my0; base < my1; base += ngroups) {
         const int64_t p = base + grp;
@@ -106,7 +108,7 @@ __device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ng
                         if (pcol[u] >= 0) acc -= pval[u] * __ldcg(a.xp + (int64_t)pcol[u] * nrhs + k);
                     q += PF * ln.EL;
                 } else {
-                    acc = bpart(a, p, row, k, ln);
+                    acc = PRE ? (ln.el == 0 ? __ldcg(a.xp + p * nrhs + k) : T(0)) : bpart(a, p, row, k, ln);
                 }
                 for (; q < c1; q += ln.EL) acc -= a.cval[q] * __ldcg(a.xp + (int64_t)a.ccol[q] * nrhs + k);
             }
@@ -122,9 +124,9 @@ __device__ bool wide_rows_general(const SolveArgs<T>& a, const Lanes& ln, int ng
 
 // Wide level, one right-hand side, one lane per row: the first row is prepared before
 // the wait; coefficients come in chunks of four whose gathers are in flight together.
-template <typename T>
+template <typename T, bool PRE = false>
 __device__ __forceinline__ T row_1rhs(const SolveArgs<T>& a, int64_t p, int32_t row, int c0, int c1, T acc) {
-    if (a.eptr) {
+    if (!PRE && a.eptr) {
         const int e1 = __ldcs(a.eptr + p + 1);
         for (int q = __ldcs(a.eptr + p); q < e1; q += 4) {
             int ec[4];
@@ -174,13 +176,13 @@ __device__ __forceinline__ T row_1rhs(const SolveArgs<T>& a, int64_t p, int32_t 
     return acc;
 }
 
-template <typename T, typename WaitFn>
+template <typename T, typename WaitFn, bool PRE = false>
 __device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, WaitFn wait) {
     const int64_t pf = my0 + threadIdx.x;
     const bool act0 = pf < my1;
     const int32_t row0 = act0 ? __ldcs(a.perm + pf) : 0;
     const int f0 = act0 ? __ldcs(a.cptr + pf) : 0, f1 = act0 ? __ldcs(a.cptr + pf + 1) : 0;
-    T pre = act0 ? __ldcs(a.dinv + pf) * __ldcs(a.b + row0) : T(0);
+    T pre = act0 ? (PRE ? __ldcg(a.xp + pf) : __ldcs(a.dinv + pf) * __ldcs(a.b + row0)) : T(0);
     int32_t pcol[PF];
     T pval[PF];
 #pragma unroll
@@ -198,13 +200,14 @@ __device__ bool wide_rows_1rhs(const SolveArgs<T>& a, int64_t my0, int64_t my1, 
 #pragma unroll
         for (int u = 0; u < PF; ++u)
             if (f0 + u < f1) acc -= pval[u] * xv[u];
-        acc = row_1rhs(a, pf, row0, f0 + PF < f1 ? f0 + PF : f1, f1, acc);
+        acc = row_1rhs<T, PRE>(a, pf, row0, f0 + PF < f1 ? f0 + PF : f1, f1, acc);
         __stcg(a.xp + pf, acc);
         a.x[row0] = acc;
     }
     for (int64_t p = pf + blockDim.x; p < my1; p += blockDim.x) {
         const int32_t row = __ldcs(a.perm + p);
-        const T acc = row_1rhs(a, p, row, __ldcs(a.cptr + p), __ldcs(a.cptr + p + 1), __ldcs(a.dinv + p) * __ldcs(a.b + row));
+        const T b0 = PRE ? __ldcg(a.xp + p) : __ldcs(a.dinv + p) * __ldcs(a.b + row);
+        const T acc = row_1rhs<T, PRE>(a, p, row, __ldcs(a.cptr + p), __ldcs(a.cptr + p + 1), b0);
         __stcg(a.xp + p, acc);
         __stcs(a.x + row, acc);
     }
@@ -355,7 +358,7 @@ __global__ void __launch_bounds__(256) k_bparts(SolveArgs<T> a, int nblocks) {
     for (int bi = me; bi < nblocks; bi += parts) {
         const int4 bd = a.blocks[bi];
         for (int64_t p = bd.x + threadIdx.x; p < bd.y; p += blockDim.x) {
-            const int e0 = a.eptr[p], e1 = a.eptr[p + 1];
+            const int e0 = a.eptr ? a.eptr[p] : 0, e1 = a.eptr ? a.eptr[p + 1] : 0;
             if (e1 - e0 > LONG) continue;
             const int32_t row = a.perm[p];
             const T di = a.dinv[p];
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(256) k_bparts(SolveArgs<T> a, int nblocks) {
                 __stcg(a.xp + p * nrhs + k, acc);
             }
         }
-        for (int64_t base = bd.x + (int64_t)warp * 32; base < bd.y; base += (int64_t)nwarps * 32) {
+        for (int64_t base = bd.x + (int64_t)warp * 32; base < bd.y && a.eptr; base += (int64_t)nwarps * 32) {
             const int64_t pl = base + lane;
             const bool lng = pl < bd.y && a.eptr[pl + 1] - a.eptr[pl] > LONG;
             unsigned mk = __ballot_sync(0xffffffffu, lng);
@@ -529,14 +532,64 @@ __device__ bool wide_rows_tiled(const SolveArgs<T>& a, int64_t my0, int64_t my1,
 
 // the rows [my0, my1) of one level with lanes-per-row wl (0: the schedule's), `wait` taken after the
 // first row's independent data is in registers
-template <typename T, typename WaitFn>
+template <typename T, typename WaitFn, bool PRE = false>
 __device__ __forceinline__ bool level_rows(const SolveArgs<T>& a, const Lanes& ln, int wl, int64_t my0, int64_t my1,
                                            WaitFn wait) {
     if (wl <= 0) wl = a.lpr;
-    if (a.nrhs == 1 && wl == 1) return wide_rows_1rhs(a, my0, my1, wait);
-    if (wl == a.lpr) return wide_rows_general(a, ln, (int)blockDim.x / a.lpr, (int)threadIdx.x / a.lpr, my0, my1, wait);
+    if (a.nrhs == 1 && wl == 1) return wide_rows_1rhs<T, WaitFn, PRE>(a, my0, my1, wait);
+    if (wl == a.lpr)
+        return wide_rows_general<T, WaitFn, PRE>(a, ln, (int)blockDim.x / a.lpr, (int)threadIdx.x / a.lpr, my0, my1,
+                                                 wait);
     const Lanes lw = make_lanes(wl, a.nrhs);
-    return wide_rows_general(a, lw, (int)blockDim.x / wl, (int)threadIdx.x / wl, my0, my1, wait);
+    return wide_rows_general<T, WaitFn, PRE>(a, lw, (int)blockDim.x / wl, (int)threadIdx.x / wl, my0, my1, wait);
+}
+
+// Thread 0's L2 prefetch of the row data of a CLUSTER segment, PD levels ahead, in three steps over
+// three levels: the level pointer of level l + PD (loaded), then the CTA's share of it -- its
+// positions' arrays prefetched and its coefficient range loaded -- then that coefficient range
+// prefetched.  Every value is used one level after its load, so thread 0 does not wait on it.
+struct ClusterPrefetch {
+    int64_t q_lo = 0, q_hi = 0;  // level pointer of the level two steps behind
+    int c_lo = 0, c_hi = 0;      // coefficient range of the share one step behind
+    bool have_q = false, have_c = false;
+};
+constexpr int CL_PD = 4;
+
+__device__ __forceinline__ void l2_prefetch_1(const void* p, int64_t bytes) {
+    // one thread: the 16-byte aligned interior of [p, p + bytes) in 4 KB pieces
+    const uint64_t a0 = ((uint64_t)p + 15) & ~(uint64_t)15, e = ((uint64_t)p + (uint64_t)bytes) & ~(uint64_t)15;
+    for (uint64_t q = a0; q < e; q += 4096) {
+        const uint32_t n = (uint32_t)(e - q < 4096 ? e - q : 4096);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void cluster_prefetch_step(const SolveArgs<T>& a, ClusterPrefetch& pf, int l, int lend,
+                                                      int me) {
+    if (pf.have_c && pf.c_hi > pf.c_lo) {
+        l2_prefetch_1(a.ccol + pf.c_lo, (int64_t)(pf.c_hi - pf.c_lo) * 4);
+        l2_prefetch_1(a.cval + pf.c_lo, (int64_t)(pf.c_hi - pf.c_lo) * (int64_t)sizeof(T));
+    }
+    pf.have_c = false;
+    if (pf.have_q) {
+        const int chunk = ((int)(pf.q_hi - pf.q_lo) + a.csize - 1) / a.csize;
+        const int64_t s0 = min(pf.q_hi, pf.q_lo + (int64_t)me * chunk), s1 = min(pf.q_hi, s0 + chunk);
+        if (s1 > s0) {
+            l2_prefetch_1(a.perm + s0, (s1 - s0) * 4);
+            l2_prefetch_1(a.cptr + s0, (s1 - s0 + 1) * 4);
+            l2_prefetch_1(a.xp + s0 * a.nrhs, (s1 - s0) * a.nrhs * (int64_t)sizeof(T));
+            pf.c_lo = a.cptr[s0];
+            pf.c_hi = a.cptr[s1];
+            pf.have_c = true;
+        }
+    }
+    const int lq = l + CL_PD;
+    pf.have_q = lq < lend;
+    if (pf.have_q) {
+        pf.q_lo = a.lptr[lq];
+        pf.q_hi = a.lptr[lq + 1];
+    }
 }
 
 // A CTA whose bounded wait ran out ("dead": the status word is set) does no more work and no more
@@ -640,7 +693,9 @@ __global__ void __launch_bounds__(512, MODE == 2 ? 1 : 2) k_solve(SolveArgs<T> a
             } else {
                 // WIDE: one level over CTAs 0..parts-1; CLUSTER: levels [y, z), each over the cluster
                 const int la = sg.y, lb = CL && type == SEG_CLUSTER ? sg.z : sg.y + 1;
+                ClusterPrefetch cpf;
                 for (int l = la; l < lb; ++l) {
+                    if (type == SEG_CLUSTER && threadIdx.x == 0 && !dead) cluster_prefetch_step(a, cpf, l, lb, me);
                     const bool barrier_entry = l != la || (region && !first);
                     const bool was_dead = dead;
                     auto w = [&a, s, barrier_entry, was_dead]() -> bool {
@@ -653,7 +708,10 @@ __global__ void __launch_bounds__(512, MODE == 2 ? 1 : 2) k_solve(SolveArgs<T> a
                     const int64_t p0 = a.lptr[l], p1 = a.lptr[l + 1];
                     const int chunk = type == SEG_WIDE ? sg.z : ((int)(p1 - p0) + a.csize - 1) / a.csize;
                     const int64_t my0 = min(p1, p0 + (int64_t)me * chunk), my1 = min(p1, my0 + chunk);
-                    const bool ok = was_dead ? (w(), false) : level_rows(a, ln, wl, my0, my1, w);
+                    const bool ok = was_dead ? (w(), false)
+                                    : (type == SEG_CLUSTER && a.pre_cl)
+                                        ? level_rows<T, decltype(w), true>(a, ln, wl, my0, my1, w)
+                                        : level_rows(a, ln, wl, my0, my1, w);
                     if (!ok) dead = true;
                     else if (a.stamps && threadIdx.x == 0) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
                     if (region && (l + 1 < lb || !last)) cluster_arrive();

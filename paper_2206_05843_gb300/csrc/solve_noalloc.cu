@@ -87,6 +87,7 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
     a.stage_rows = sc.stage_rows;
     a.stage_entries = sc.stage_entries;
     a.pre = sc.pre;
+    a.pre_cl = sc.pre_cl;
     a.csize = sc.csize;
     a.tile_ecap = sc.tile_ecap;
     SP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));

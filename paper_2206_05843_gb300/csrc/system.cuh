@@ -61,6 +61,7 @@ struct Schedule {
     int runs = 0;      // RUN segments (0: the wide-only kernel variant, no shared memory)
     int64_t tiled_levels = 0;
     int pre_grid = 0;  // its CTAs
+    int pre_cl = 0;    // the b-part kernel also covers the rows of CLUSTER segments (ranges after the run blocks)
     size_t smem = 0;
     int64_t run_levels = 0;
     std::vector<int4> h_segs, h_blocks;
@@ -99,6 +100,7 @@ struct SolveArgs {
     int tile_ecap;  // coefficients one tile buffer holds (0: no tiled WIDE segments)
     int stage_rows, stage_entries;
     int pre;        // xp holds the b-parts of the staged blocks' rows (k_bparts ran first)
+    int pre_cl;     // and of the CLUSTER segments' rows
 };
 
 }  // namespace sp
