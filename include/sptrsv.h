@@ -199,6 +199,9 @@ typedef struct {
     int64_t tiled_levels;  /* WIDE levels whose coefficients stream through shared-memory tiles */
     int32_t tiles_setting; /* the system's tile knob (0 automatic, 1 never) */
     int32_t reserved0;
+    int64_t shared_x_levels; /* CLUSTER levels whose x the next level reads from the cluster's shared memory */
+    int32_t shared_x_setting; /* the system's shared-x knob (0 automatic, 1 never) */
+    int32_t reserved1;
 } sptrsv_system_info;
 
 sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info* out_host);
@@ -287,8 +290,12 @@ sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_wi
  * cluster (2..16; 0: automatic, 16; 1: no clusters), one cluster barrier per level instead of a
  * device-wide handoff.  tiles 0 (automatic): without clusters, WIDE levels of one right-hand side
  * stream their coefficients through shared memory in tiles (bulk copies, double-buffered) when
- * they fit; tiles 1: never.  Negative values keep the current setting.  No stream work. */
-sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows, int32_t tiles);
+ * they fit; tiles 1: never.  shared_x 0 (automatic): CLUSTER segments of one right-hand side keep each
+ * level's x in the shared memory of the CTA that computed it, where the next level reads it across
+ * the cluster (the global copy is written after the level's barrier); shared_x 1: never.  Negative
+ * values keep the current setting.  No stream work. */
+sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows, int32_t tiles,
+                                         int32_t shared_x);
 
 /* Autotuner: times candidate solves (b = 0) over lanes per row and the widest level
  * executed inside a single-CTA run, keeps the fastest for nrhs right-hand sides and

@@ -71,7 +71,8 @@ class SystemInfo(C.Structure):
                 ("launches", C.c_int32), ("ctas", C.c_int32), ("candidate_us", C.c_double * 4),
                 ("cluster", C.c_int32), ("cluster_setting", C.c_int32), ("cluster_levels", C.c_int64),
                 ("cluster_rows", C.c_int64), ("tiled_levels", C.c_int64), ("tiles_setting", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("reserved0", C.c_int32), ("shared_x_levels", C.c_int64), ("shared_x_setting", C.c_int32),
+                ("reserved1", C.c_int32)]
 
 
 class BatchInfo(C.Structure):
@@ -110,7 +111,7 @@ def load():
             "sptrsv_debug_set_wait": [vp, i64, i64],
             "sptrsv_debug_run_blocks": [vp, i64, vp, i32, i32, i32, vp, i64, vp, vp],
             "sptrsv_system_tune": [vp, i32, i32, i32],
-            "sptrsv_system_tune_cluster": [vp, i32, i64, i32],
+            "sptrsv_system_tune_cluster": [vp, i32, i64, i32, i32],
             "sptrsv_system_autotune": [vp, i32, vp, vp],
             "sptrsv_upper_to_lower": [vp, vp, vp, vp, vp],
             "sptrsv_system_reverse_rows": [vp, vp],
@@ -315,10 +316,12 @@ class System:
     def tune(self, block=0, run_width=0, lanes_per_row=0):
         check(load().sptrsv_system_tune(self.h, block, run_width, lanes_per_row))
 
-    def tune_cluster(self, cluster=-1, cluster_rows=-1, tiles=-1):
-        """CTAs per cluster for mid-width levels (0 automatic, 1 none), the widest such level, and
-        whether wide levels may stream through shared-memory tiles (0 automatic, 1 never)."""
-        check(load().sptrsv_system_tune_cluster(self.h, cluster, cluster_rows, tiles))
+    def tune_cluster(self, cluster=-1, cluster_rows=-1, tiles=-1, shared_x=-1):
+        """CTAs per cluster for mid-width levels (0 automatic, 1 none), the widest such level,
+        whether wide levels may stream through shared-memory tiles (0 automatic, 1 never), and
+        whether cluster levels read the previous level's x from the cluster's shared memory
+        (0 automatic, 1 never).  -1 keeps a setting."""
+        check(load().sptrsv_system_tune_cluster(self.h, cluster, cluster_rows, tiles, shared_x))
 
     def autotune(self, nrhs=1) -> float:
         """Times candidate schedules and keeps the fastest; returns its time in us."""

@@ -54,6 +54,7 @@ sptrsv_status launch_solve(sptrsv_system* s, const void* b, void* x, int nrhs, i
     a.pre = sc.pre;
     a.pre_cl = sc.pre_cl;
     a.csize = sc.csize;
+    a.dsm_cap = sc.dsm_cap;
     a.tile_ecap = sc.tile_ecap;
 
     SP_CUDA(cudaMemsetAsync(s->flags.p, 0xff, (size_t)sc.grid * sizeof(int), st));
@@ -233,7 +234,8 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
         return SPTRSV_ERR_INVALID;
     }
     if (sc.nrhs == nrhs && sc.lpr == lpr && sc.block == block && sc.run_width == s->run_width &&
-        sc.cluster == s->cluster && sc.cluster_rows == s->cluster_rows && sc.tiles == s->tiles && sc.segs.p)
+        sc.cluster == s->cluster && sc.cluster_rows == s->cluster_rows && sc.tiles == s->tiles &&
+        sc.shared_x == s->shared_x && sc.segs.p)
         return SPTRSV_OK;
     const int ngroups = block / lpr;
     // shared memory: two staging buffers + an x ring of at least twice the staged rows
@@ -310,8 +312,27 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
         csize = 1;
     }
     if (csize > 1) tiles_ok = false;
+    // cluster levels of one right-hand side keep their x in shared memory (two ring slots of the
+    // widest CTA share), when the larger shared memory still leaves a whole cluster co-resident;
+    // their b-parts are then computed up front (pre_cl below: one right-hand side always qualifies)
+    sc.dsm_cap = 0;
+    size_t smem_cl = smem;
+    if (csize > 1 && nrhs == 1 && s->shared_x != 1) {
+        int64_t cap = 0;
+        for (int64_t q = 0; q < m; ++q)
+            if (kind[q] == 1) cap = std::max<int64_t>(cap, (lp[q + 1] - lp[q] + csize - 1) / csize);
+        const size_t ring = align16((size_t)(2 * cap * vb));
+        int64_t g2 = gcl;
+        if (ring > smem) SP_TRY(capacity(ring, csize, 0, &g2));
+        if (cap > 0 && g2 >= csize) {
+            sc.dsm_cap = (int)cap;
+            smem_cl = std::max(smem, ring);
+            gcl = g2;
+        }
+    }
     const int64_t gmax = csize > 1 ? gcl : gplain;
     sc.cluster_levels = 0;
+    sc.dsm_levels = 0;
     int64_t l = 0;
     while (l < m) {
         if (kind[l] == 1) {
@@ -321,8 +342,11 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
             const int64_t rows = lp[l1] - lp[l];
             // lanes per row of the segment: two for single right-hand sides of 4 or more coefficients
             const int wl = (nrhs == 1 && lpr == 1 && ents >= 4 * rows) ? 2 : lpr;
-            sc.h_segs.push_back(make_int4(SEG_CLUSTER | (wl == lpr ? 0 : wl << SEG_LPR_SHIFT), (int)l, (int)l1, csize));
+            const int dsm = sc.dsm_cap > 0 ? SEG_DSM : 0;
+            sc.h_segs.push_back(
+                make_int4(SEG_CLUSTER | dsm | (wl == lpr ? 0 : wl << SEG_LPR_SHIFT), (int)l, (int)l1, csize));
             sc.cluster_levels += l1 - l;
+            if (dsm) sc.dsm_levels += l1 - l;
             max_parts = std::max<int64_t>(max_parts, csize);
             l = l1;
             continue;
@@ -423,6 +447,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     sc.cluster = s->cluster;
     sc.cluster_rows = s->cluster_rows;
     sc.tiles = s->tiles;
+    sc.shared_x = s->shared_x;
     sc.nrhs = nrhs;
     sc.lpr = lpr;
     sc.block = block;
@@ -432,7 +457,7 @@ sptrsv_status prepare_schedule(sptrsv_system* s, int nrhs) {
     sc.stage_entries = stage_entries;
     sc.runs = 0;
     for (const int4& sg : sc.h_segs) sc.runs += (sg.x & SEG_TYPE_MASK) == SEG_RUN;
-    sc.smem = sc.tile_ecap > 0 ? std::max(smem, 2 * tile_buf_bytes(sc.tile_ecap, vb)) : smem;
+    sc.smem = sc.tile_ecap > 0 ? std::max(smem, 2 * tile_buf_bytes(sc.tile_ecap, vb)) : (csize > 1 ? smem_cl : smem);
     if (csize == 1 && sc.tile_ecap == 0 && sc.runs == 0) sc.smem = 0;  // wide levels only: no staging
     SP_TRY(s->flags.ensure((size_t)std::max(1, sc.grid)));
     SP_TRY(s->status.ensure(1));

@@ -592,6 +592,214 @@ __device__ __forceinline__ void cluster_prefetch_step(const SolveArgs<T>& a, Clu
     }
 }
 
+// ---------------------------------------------------------------------------------
+// CLUSTER segments with x in the cluster's shared memory
+// ---------------------------------------------------------------------------------
+
+// One CTA's share of level l: rows [my0, my1), chunks of ceil(width / csize) rows
+struct ClShare {
+    int64_t p0, my0, my1;
+    int chunk;
+};
+template <typename T>
+__device__ __forceinline__ ClShare cl_share(const SolveArgs<T>& a, int l, int me) {
+    ClShare c;
+    c.p0 = a.lptr[l];
+    const int64_t p1 = a.lptr[l + 1];
+    c.chunk = ((int)(p1 - c.p0) + a.csize - 1) / a.csize;
+    c.my0 = min(p1, c.p0 + (int64_t)me * c.chunk);
+    c.my1 = min(p1, c.my0 + c.chunk);
+    return c;
+}
+
+// the x value of position q: from the shared memory of the CTA that computed it when q is on the previous
+// level of the segment (owner (q - pp0) / pchunk, ring slot `slot`), else from L2
+template <typename T>
+__device__ __forceinline__ T cl_x(const SolveArgs<T>& a, int32_t q, bool prev_ok, int64_t pp0, int pchunk,
+                                  uint32_t ring_base, int slot) {
+    if (prev_ok && q >= pp0) {
+        const int rel = (int)(q - pp0);
+        const int owner = rel / pchunk;
+        const uint32_t local = ring_base + (uint32_t)((slot * a.dsm_cap + (rel - owner * pchunk)) * (int)sizeof(T));
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(owner));
+        if (sizeof(T) == 8) {
+            double d;
+            asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(d) : "r"(remote) : "memory");
+            return (T)d;
+        } else {
+            float f;
+            asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(f) : "r"(remote) : "memory");
+            return (T)f;
+        }
+    }
+    return __ldcg(a.xp + q);
+}
+
+// One CTA's share of a level from its two level pointers (registers, no loads)
+struct DsmShare {
+    int32_t p0, my0, my1, chunk;
+};
+__device__ __forceinline__ DsmShare dsm_share(int32_t l0, int32_t l1, int csize, int me) {
+    DsmShare c;
+    c.p0 = l0;
+    c.chunk = (l1 - l0 + csize - 1) / csize;
+    c.my0 = min(l1, l0 + me * c.chunk);
+    c.my1 = min(l1, c.my0 + c.chunk);
+    return c;
+}
+
+// the first row of a thread's share of a level, loaded ahead of the level's barrier in two stages:
+// its row, row pointers and b-part two levels ahead, its first DSM_PF coefficients one level ahead
+constexpr int DSM_PF = 4;
+template <typename T>
+struct DsmHead {
+    int32_t p, row, f0, f1;
+    T bp;
+};
+template <typename T>
+struct DsmRow {
+    DsmHead<T> h;
+    int32_t pc[DSM_PF];
+    T pv[DSM_PF];
+};
+template <typename T>
+__device__ __forceinline__ DsmHead<T> dsm_load_head(const SolveArgs<T>& a, int32_t p, bool act) {
+    DsmHead<T> h;
+    h.p = act ? p : -1;
+    h.row = act ? __ldcs(a.perm + p) : 0;
+    h.f0 = act ? __ldcs(a.cptr + p) : 0;
+    h.f1 = act ? __ldcs(a.cptr + p + 1) : 0;
+    h.bp = act ? __ldcg(a.xp + p) : T(0);
+    return h;
+}
+template <typename T>
+__device__ __forceinline__ void dsm_load_coefs(const SolveArgs<T>& a, const DsmHead<T>& h, DsmRow<T>& r) {
+    r.h = h;
+#pragma unroll
+    for (int j = 0; j < DSM_PF; ++j) {
+        const bool ok = h.f0 + j < h.f1;
+        r.pc[j] = ok ? __ldcs(a.ccol + h.f0 + j) : 0;
+        r.pv[j] = ok ? __ldcs(a.cval + h.f0 + j) : T(0);
+    }
+}
+
+// A whole SEG_DSM segment, levels [la, lb), for one CTA of cluster 0, one lane per row.  Level l: wait
+// (the segment's entry, or the cluster barrier of level l-1); every row of the CTA's share reads its
+// dependencies on level l-1 from the cluster's shared memory and older ones from L2 (four partial sums,
+// so that a long row's float64 chain is a quarter as long), and leaves its x in this CTA's ring slot
+// (l - la) & 1; arrive.  After the arrive (whose release would otherwise wait for these loads): the
+// first row of level l+1 loads its first coefficients, the first row of level l+2 its row data, the
+// level pointer of level l+4 comes in (so that no load waits on another one inside a level), the CTA's
+// last thread prefetches the data of later levels to L2, and the level's x goes to xp and x in global
+// memory -- the next level reads it from shared memory, later levels after later barriers.  On the
+// segment's last level the global stores come before the arrive (the next segment reads global memory),
+// and a closing cluster barrier at the region's end keeps every CTA until no other CTA reads its shared
+// memory.  The rows' b-parts (E rows included) are in xp already (the schedule computes them up front
+// for every CLUSTER segment of one right-hand side).  A dead CTA still takes every barrier.  Returns
+// false when the entry wait ran out.
+template <typename T, typename EnterFn>
+__device__ bool cluster_segment_dsm(const SolveArgs<T>& a, int la, int lb, bool last, int me, bool dead,
+                                    EnterFn enter) {
+    const uint32_t ring_base = smem_addr(g_dyn_smem);
+    T* ring = (T*)g_dyn_smem;
+    const int t = threadIdx.x;
+    const int cs = a.csize;
+    const bool pf_thread = t == (int)blockDim.x - 1;
+    ClusterPrefetch cpf;
+    // level pointers lptr[l .. l+3] (entries past lb repeat lptr[lb]; they describe no rows)
+    int32_t L0 = a.lptr[la], L1 = a.lptr[la + 1];
+    int32_t L2 = la + 2 <= lb ? a.lptr[la + 2] : L1;
+    int32_t L3 = la + 3 <= lb ? a.lptr[la + 3] : L2;
+    DsmShare sh = dsm_share(L0, L1, cs, me);
+    DsmRow<T> cur;
+    dsm_load_coefs(a, dsm_load_head(a, sh.my0 + t, sh.my0 + t < sh.my1), cur);
+    DsmShare sh1 = dsm_share(L1, L2, cs, me);
+    DsmHead<T> nxt = dsm_load_head(a, sh1.my0 + t, la + 1 < lb && sh1.my0 + t < sh1.my1);
+    int32_t L4 = la + 4 <= lb ? a.lptr[la + 4] : L3;
+    if (pf_thread && !dead) cluster_prefetch_step(a, cpf, la, lb, me);
+    int32_t pp0 = 0;
+    int pchunk = 1;
+    for (int l = la; l < lb; ++l) {
+        const int slot = (l - la) & 1;
+        if (l == la) dead = !enter() || dead;
+        else cluster_wait();
+        const bool prev_ok = l > la;
+        if (!dead) {
+            // the thread's rows of the share: the first from registers, the others loaded here
+            for (int32_t q = sh.my0 + t; q < sh.my1; q += blockDim.x) {
+                const bool first = q == cur.h.p;
+                const int32_t r = first ? cur.h.row : __ldcs(a.perm + q);
+                const int c0 = first ? cur.h.f0 : __ldcs(a.cptr + q), c1 = first ? cur.h.f1 : __ldcs(a.cptr + q + 1);
+                T sum[4] = {first ? cur.h.bp : __ldcg(a.xp + q), T(0), T(0), T(0)};
+                int u = c0;
+                if (first) {
+                    T xv[DSM_PF];
+#pragma unroll
+                    for (int j = 0; j < DSM_PF; ++j)
+                        xv[j] = c0 + j < c1 ? cl_x(a, cur.pc[j], prev_ok, pp0, pchunk, ring_base, slot ^ 1) : T(0);
+#pragma unroll
+                    for (int j = 0; j < DSM_PF; ++j)
+                        if (c0 + j < c1) sum[j & 3] -= cur.pv[j] * xv[j];
+                    u = c0 + DSM_PF;
+                }
+                for (; u < c1; u += 4) {
+                    int32_t cc[4];
+                    T cv[4], xv[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool ok = u + j < c1;
+                        cc[j] = ok ? __ldcs(a.ccol + u + j) : 0;
+                        cv[j] = ok ? __ldcs(a.cval + u + j) : T(0);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        xv[j] = u + j < c1 ? cl_x(a, cc[j], prev_ok, pp0, pchunk, ring_base, slot ^ 1) : T(0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (u + j < c1) sum[j] -= cv[j] * xv[j];
+                }
+                const T acc = (sum[0] + sum[1]) + (sum[2] + sum[3]);
+                ring[slot * a.dsm_cap + (q - sh.my0)] = acc;
+                if (l + 1 == lb) {  // the segment's last level: global memory before the arrive
+                    __stcg(a.xp + q, acc);
+                    a.x[r] = acc;
+                }
+            }
+        }
+        if (l + 1 < lb || !last) cluster_arrive();
+        // loads for later levels, independent of x
+        const int32_t p_l = cur.h.p, row_l = cur.h.row;
+        dsm_load_coefs(a, nxt, cur);  // level l+1
+        const DsmShare sh2 = dsm_share(L2, L3, cs, me);
+        nxt = dsm_load_head(a, sh2.my0 + t, l + 2 < lb && sh2.my0 + t < sh2.my1);  // level l+2
+        const int32_t L5 = l + 5 <= lb ? a.lptr[l + 5] : L4;
+        if (pf_thread && !dead && l + 1 < lb) cluster_prefetch_step(a, cpf, l + 1, lb, me);
+        if (!dead && l + 1 < lb) {
+            // this thread's own values of the level (no other thread wrote them)
+            for (int32_t q = sh.my0 + t; q < sh.my1; q += blockDim.x) {
+                const T v = ring[slot * a.dsm_cap + (q - sh.my0)];
+                __stcg(a.xp + q, v);
+                __stcs(a.x + (q == p_l ? row_l : __ldcs(a.perm + q)), v);
+            }
+        }
+        if (a.stamps && t == 0 && !dead) atomicMax(a.stamps + l, (unsigned long long)globaltimer());
+        pp0 = sh.p0;
+        pchunk = max(1, sh.chunk);
+        sh = dsm_share(L1, L2, cs, me);
+        L1 = L2;
+        L2 = L3;
+        L3 = L4;
+        L4 = L5;
+    }
+    if (last) {
+        // no CTA leaves while another may still read its ring
+        cluster_arrive();
+        cluster_wait();
+    }
+    return !dead;
+}
+
 // A CTA whose bounded wait ran out ("dead": the status word is set) does no more work and no more
 // flag waits, and publishes nothing, so that the CTAs waiting on it run out too; inside a cluster
 // region it still takes every cluster barrier, so that no CTA of its cluster waits on it forever.
@@ -690,6 +898,17 @@ __global__ void __launch_bounds__(512, MODE == 2 ? 1 : 2) k_solve(SolveArgs<T> a
                 }
                 if (!ok) dead = true;
                 if (region && !last) cluster_arrive();
+            } else if (type == SEG_CLUSTER && (sg.x & SEG_DSM)) {
+                // the whole segment with x in the cluster's shared memory
+                const bool was_dead = dead;
+                auto enter = [&a, s, first, was_dead]() -> bool {
+                    if (!first) {
+                        cluster_wait();
+                        return !was_dead;
+                    }
+                    return was_dead ? false : wait_segment(a, s - 1);
+                };
+                dead = !cluster_segment_dsm<T>(a, sg.y, sg.z, last, me, dead, enter);
             } else {
                 // WIDE: one level over CTAs 0..parts-1; CLUSTER: levels [y, z), each over the cluster
                 const int la = sg.y, lb = CL && type == SEG_CLUSTER ? sg.z : sg.y + 1;

@@ -89,6 +89,7 @@ sptrsv_status launch_noalloc(const sptrsv_system* s, const void* b, void* x, int
     a.pre = sc.pre;
     a.pre_cl = sc.pre_cl;
     a.csize = sc.csize;
+    a.dsm_cap = sc.dsm_cap;
     a.tile_ecap = sc.tile_ecap;
     SP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
     if (sc.run_width == -2) {

@@ -229,6 +229,9 @@ sptrsv_status sptrsv_system_info_get(const sptrsv_system* s, sptrsv_system_info*
     o->tiled_levels = sc.segs.p ? sc.tiled_levels : 0;
     o->tiles_setting = s->tiles;
     o->reserved0 = 0;
+    o->shared_x_levels = sc.segs.p ? sc.dsm_levels : 0;
+    o->shared_x_setting = s->shared_x;
+    o->reserved1 = 0;
     return SPTRSV_OK;
 }
 
@@ -315,13 +318,19 @@ sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_wi
     return SPTRSV_OK;
 }
 
-sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows, int32_t tiles) {
+sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows, int32_t tiles,
+                                         int32_t shared_x) {
     if (!s) { set_error("system_tune_cluster: null system"); return SPTRSV_ERR_INVALID; }
     if (cluster > 16) { set_error("system_tune_cluster: at most 16 CTAs per cluster"); return SPTRSV_ERR_INVALID; }
     if (tiles > 1) { set_error("system_tune_cluster: tiles must be 0 (automatic) or 1 (never)"); return SPTRSV_ERR_INVALID; }
+    if (shared_x > 1) {
+        set_error("system_tune_cluster: shared_x must be 0 (automatic) or 1 (never)");
+        return SPTRSV_ERR_INVALID;
+    }
     if (cluster >= 0) s->cluster = cluster;
     if (cluster_rows >= 0) s->cluster_rows = cluster_rows;
     if (tiles >= 0) s->tiles = tiles;
+    if (shared_x >= 0) s->shared_x = shared_x;
     s->sched.nrhs = -1;  // rebuild on the next solve
     return SPTRSV_OK;
 }

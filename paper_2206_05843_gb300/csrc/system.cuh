@@ -18,6 +18,9 @@ constexpr int SEG_REGION = 1 << 16, SEG_FIRST = 1 << 17, SEG_LAST = 1 << 18;
 // A WIDE segment of one right-hand side whose coefficients stream through shared memory in tiles of
 // TILE_ROWS >> ((x >> SEG_TILE_SHIFT) & 3) rows (bulk copies, double-buffered): SEG_TILED
 constexpr int SEG_TILED = 1 << 19, SEG_TILE_SHIFT = 20;
+// A CLUSTER segment of one right-hand side whose levels keep their x in the CTAs' shared memory (a
+// two-level ring), read across the cluster by the next level: SEG_DSM
+constexpr int SEG_DSM = 1 << 22;
 constexpr int TILE_ROWS = 512;   // rows of a tile at the largest size (one per thread of a 512-thread CTA)
 constexpr int TILE_MAX = 64;     // tiles of one CTA's share of a level
 constexpr int64_t TILE_SMEM_MAX = 100 * 1024;  // shared memory the two tile buffers may take (2 CTAs per SM)
@@ -53,6 +56,8 @@ struct Schedule {
     int csize = 1;          // CTAs per cluster of the launch (1: no cluster segments, plain launch)
     int cluster = 0;        // the system's cluster setting the schedule was built with
     int tiles = 0;          // the system's tile setting the schedule was built with
+    int shared_x = 0;       // and its shared-x setting
+    int64_t dsm_levels = 0; // levels of SEG_DSM segments
     int64_t cluster_rows = 0;  // widest level run as a CLUSTER level
     int64_t cluster_levels = 0;  // levels executed in CLUSTER segments
     int stage_rows = 0, stage_entries = 0;
@@ -62,6 +67,7 @@ struct Schedule {
     int64_t tiled_levels = 0;
     int pre_grid = 0;  // its CTAs
     int pre_cl = 0;    // the b-part kernel also covers the rows of CLUSTER segments (ranges after the run blocks)
+    int dsm_cap = 0;   // rows per CTA and level of the SEG_DSM segments' shared-memory ring slots
     size_t smem = 0;
     int64_t run_levels = 0;
     std::vector<int4> h_segs, h_blocks;
@@ -101,6 +107,7 @@ struct SolveArgs {
     int stage_rows, stage_entries;
     int pre;        // xp holds the b-parts of the staged blocks' rows (k_bparts ran first)
     int pre_cl;     // and of the CLUSTER segments' rows
+    int dsm_cap;    // rows of one level a CTA keeps in shared memory in SEG_DSM segments (one ring slot)
 };
 
 }  // namespace sp
@@ -120,6 +127,7 @@ struct sptrsv_system {
     int block = 512, run_width = 0, lpr = 0;  // 0: automatic
     int cluster = 0;          // CTAs of the cluster that runs mid-width levels: 0 automatic, 1 none, 2..16
     int tiles = 0;            // wide levels through shared-memory tiles: 0 automatic, 1 never
+    int shared_x = 0;         // cluster levels exchange x through shared memory: 0 automatic, 1 never
     int64_t cluster_rows = 0; // widest level run on the cluster (0: automatic)
     sp::Schedule sched;
     std::vector<int32_t> h_cptr;  // host copy of cptr, for cutting run blocks

@@ -13,14 +13,14 @@ from tests.gpu_util import TOL_F32, TOL_F64, rel_l2, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def solve_cluster(m, b, cluster, cluster_rows=0, run_width=0, lpr=0, system_kw=None, stamps=False):
+def solve_cluster(m, b, cluster, cluster_rows=0, run_width=0, lpr=0, system_kw=None, stamps=False, shared_x=0):
     torch = torch_cuda()
     M = B.Matrix.from_host(m)
     lv = B.Levels(M)
     s = B.System(M, lv, **(system_kw or {}))
     if run_width or lpr:
         s.tune(run_width=run_width, lanes_per_row=lpr)
-    s.tune_cluster(cluster, cluster_rows)
+    s.tune_cluster(cluster, cluster_rows, shared_x=shared_x)
     vt = torch.float64 if M.dtype == B.F64 else torch.float32
     bt = torch.from_numpy(np.ascontiguousarray(b)).to("cuda", dtype=vt)
     st = torch.zeros(max(s.m, 1), dtype=torch.int64, device="cuda") if stamps else None
@@ -121,6 +121,7 @@ def test_cluster_bounded_wait_times_out_without_faulting(withhold):
     s.solve(bt, check_status=True)
     info = s.refresh()
     assert info["segments"] == 3 and info["cluster_levels"] == 3  # WIDE, CLUSTER (3 levels), WIDE
+    assert info["shared_x_levels"] == 3  # x of the cluster levels through shared memory
     s.debug_set_wait(withhold_segment=withhold, timeout_ns=50_000_000)
     s.solve(bt)
     with pytest.raises(B.SptrsvError) as e:
@@ -129,3 +130,55 @@ def test_cluster_bounded_wait_times_out_without_faulting(withhold):
     s.debug_set_wait(-1, 0)
     x = s.solve(bt, check_status=True).cpu().numpy()
     assert rel_l2(x, O.forward_subst(m.rowptr, m.colidx, m.vals, b)) < TOL_F64
+
+
+@pytest.mark.parametrize("cluster", [2, 8, 16])
+def test_shared_x_grid_ragged_shares(cluster):
+    """One right-hand side: CLUSTER levels read the previous level's x from the shared memory of the
+    CTA that computed it.  Grid levels of 65..300 rows split over 2, 8 or 16 CTAs leave ragged last
+    shares (and CTAs with no rows); the solution matches the oracle and the same schedule without
+    the shared-memory exchange."""
+    m = S.gen_laplacian(300)
+    b = S.rhs_uniform(m.n, 1, 3)
+    s, x, ref, st = solve_cluster(m, b, cluster, run_width=64, stamps=True)
+    info = s.refresh()
+    assert info["shared_x_levels"] == info["cluster_levels"] > 0
+    assert rel_l2(x, ref) <= TOL_F64
+    t = st.cpu().numpy()[:s.m]
+    assert (t > 0).all() and (np.diff(t) >= 0).all()
+    s1, x1, _, _ = solve_cluster(m, b, cluster, run_width=64, shared_x=1)
+    assert s1.refresh()["shared_x_levels"] == 0 and s1.refresh()["cluster_levels"] == info["cluster_levels"]
+    assert rel_l2(x1, ref) <= TOL_F64
+
+
+@pytest.mark.parametrize("rewrite", [None, "naive", "depth4"])
+def test_shared_x_mixture_and_rewritten_rows(rewrite):
+    """Mixtures with WIDE, CLUSTER and thin levels; rewritten systems put rows with E entries (b-parts
+    computed up front) and long substituted rows into the CLUSTER levels."""
+    m = S.gen_mixture(150_000, 10_091)
+    _, b = S.rhs_from_xtrue(m, 1, 4)
+    kw = {None: {}, "naive": dict(kind=B.NAIVE, cap=1.5), "depth4": dict(kind=B.DEPTH_K, k=4)}[rewrite]
+    s, x, ref, _ = solve_cluster(m, b, 16, system_kw=kw)
+    assert s.refresh()["shared_x_levels"] > 0
+    assert rel_l2(x, ref) <= TOL_F64
+
+
+def test_shared_x_float32_profile():
+    """float32 values; CLUSTER segments after WIDE levels and after thin runs, with levels of 1,000
+    to 9,000 rows (shares of up to 563 rows: two rows for some threads)."""
+    m = layered_profile([20000, 9000, 1000, 7001, 8, 8, 8, 8, 8, 3001, 9000, 20000, 5000], 5, 17)
+    m32 = m.astype(np.float32)
+    b = S.rhs_uniform(m.n, 1, 5).astype(np.float32)
+    s, x, ref, _ = solve_cluster(m32, b, 16, cluster_rows=10000)
+    assert s.refresh()["shared_x_levels"] >= 5
+    assert rel_l2(x, ref) <= TOL_F32
+
+
+def test_shared_x_full_size_grid():
+    """The 2048 x 2048 grid (4,194,304 rows, 4,095 levels of up to 2,048 rows) at full size, plain and
+    rewritten to depth 4."""
+    m, b, _ = S.gen_config("c2")
+    for kw in ({}, dict(kind=B.DEPTH_K, k=4)):
+        s, x, ref, _ = solve_cluster(m, b, 16, system_kw=kw)
+        assert s.refresh()["shared_x_levels"] > 0
+        assert rel_l2(x, ref) <= TOL_F64
