@@ -297,9 +297,11 @@ sptrsv_status sptrsv_system_tune(sptrsv_system* s, int32_t block, int32_t run_wi
 sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int64_t cluster_rows, int32_t tiles,
                                          int32_t shared_x);
 
-/* Autotuner: times candidate solves (b = 0) over lanes per row and the widest level
- * executed inside a single-CTA run, keeps the fastest for nrhs right-hand sides and
- * caches the choice by the system's signature (n, m, stored entries, nrhs, dtype).
+/* Autotuner: times candidate solves (b = 0) over lanes per row, the widest level executed
+ * inside a single-CTA run and the level-executor knobs (clusters of 16 or 8 CTAs or none,
+ * tiles, then the widest cluster level and, for one right-hand side, the shared-x exchange
+ * on and off), keeps the fastest for nrhs right-hand sides and caches the choice by the
+ * system's signature (n, m, stored entries, nrhs, dtype).
  * *best_us_host (may be NULL) receives the best time.  Synchronizes the stream. */
 sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, double* best_us_host, sptrsv_stream_t stream);
 

@@ -495,6 +495,7 @@ struct TuneVal {
     int cluster = 0;
     int64_t cluster_rows = 0;
     int tiles = 0;
+    int shared_x = 0;
 };
 std::mutex g_stune_mu;
 std::map<TuneKey, TuneVal> g_stune_cache;
@@ -521,6 +522,7 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
             s->cluster = f->second.cluster;
             s->cluster_rows = f->second.cluster_rows;
             s->tiles = f->second.tiles;
+            s->shared_x = f->second.shared_x;
             if (best_us) *best_us = f->second.us;
             return prepare_schedule(s, nrhs);
         }
@@ -546,6 +548,8 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
     SP_CUDA(cudaEventCreate(&e1));
     TuneVal best{512, 0, 0, 1e300};
     const int old_block = s->block, old_rw = s->run_width, old_lpr = s->lpr, old_cl = s->cluster, old_tl = s->tiles;
+    const int old_sx = s->shared_x;
+    s->shared_x = 0;
     const int64_t old_clr = s->cluster_rows;
     sptrsv_status rc = SPTRSV_OK;
     // best of 3 timed solves of the current settings, in microseconds
@@ -602,6 +606,18 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
             if (rc != SPTRSV_OK) break;
             if (us < best.us) best = TuneVal{best.block, best.run_width, best.lpr, us, best.cluster, rows, best.tiles};
         }
+        // cluster levels of one right-hand side: also without the shared-memory exchange of x
+        if (rc == SPTRSV_OK && nrhs == 1) {
+            s->cluster_rows = best.cluster_rows;
+            s->shared_x = 1;
+            double us = 0;
+            rc = time_current(&us);
+            if (rc == SPTRSV_OK && us < best.us) {
+                best.us = us;
+                best.shared_x = 1;
+            }
+            s->shared_x = 0;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -612,6 +628,7 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         s->cluster = old_cl;
         s->cluster_rows = old_clr;
         s->tiles = old_tl;
+        s->shared_x = old_sx;
         s->sched.nrhs = -1;
         return rc;
     }
@@ -622,6 +639,7 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
     s->cluster = best.cluster;
     s->cluster_rows = best.cluster_rows;
     s->tiles = best.tiles;
+    s->shared_x = best.shared_x;
     s->sched.nrhs = -1;
     {
         std::lock_guard<std::mutex> lk(g_stune_mu);
