@@ -23,6 +23,12 @@
  *     sptrsv_last_error() holds a one-line message for the calling thread.
  *   - Every device-side wait is bounded; a wait that runs out sets the status
  *     SPTRSV_ERR_TIMEOUT and the kernel returns, leaving the CUDA context usable.
+ *   - The persistent solve kernel is a cooperative launch, with thread-block clusters when its
+ *     schedule has CLUSTER segments.  It checks its cluster shape on entry: a launch that runs
+ *     without it (Nsight Compute runs cooperative launches so) stops at once and the status
+ *     reads SPTRSV_ERR_CUDA.  The environment variable SPTRSV_PROFILE_LAUNCH=1, read once per
+ *     process, drops the cooperative attribute from launches with clusters, so that such a
+ *     profiler sees the kernel as it runs; the grid is sized from cluster occupancy either way.
  */
 #ifndef SPTRSV_H
 #define SPTRSV_H

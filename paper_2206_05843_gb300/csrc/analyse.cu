@@ -195,6 +195,8 @@ sptrsv_status map_dev_status(int code, const char* where) {
         case DEV_NUMERIC: set_error("%s: rewritten coefficient above the growth guard or not finite", where);
             return SPTRSV_ERR_NUMERIC;
         case DEV_OVERFLOW: set_error("%s: device scratch capacity exceeded", where); return SPTRSV_ERR_OOM;
+        case DEV_LAUNCH: set_error("%s: the solve kernel ran without its thread-block clusters", where);
+            return SPTRSV_ERR_CUDA;
         default: set_error("%s: invalid input detected on the device (code %d)", where, code);
             return SPTRSV_ERR_INVALID;
     }

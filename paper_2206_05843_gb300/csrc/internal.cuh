@@ -173,7 +173,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity, 
 #endif
 
 // status words written by kernels (device int, 0 = ok)
-enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NUMERIC = 2, DEV_OVERFLOW = 3, DEV_INVALID = 4 };
+// DEV_LAUNCH: a kernel found itself launched without the thread-block cluster shape it was built for
+enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NUMERIC = 2, DEV_OVERFLOW = 3, DEV_INVALID = 4, DEV_LAUNCH = 5 };
 
 sptrsv_status map_dev_status(int code, const char* where);
 

@@ -8,6 +8,8 @@
 // chain of thin levels executed by CTA 0 alone with the staged single-CTA executor.
 #pragma once
 
+#include <cstdlib>
+
 #include "run_exec.cuh"
 
 namespace sp {
@@ -865,6 +867,16 @@ __global__ void __launch_bounds__(512, MODE == 2 ? 1 : 2) k_solve(SolveArgs<T> a
             }
         }
     } else {
+        // the cluster shape the schedule was built for: CTAs csize apart form one cluster.  A launch
+        // without it (every CTA sees the same) records the error and ends before any CTA touches
+        // another's shared memory or waits at a cluster barrier
+        unsigned ncta, crank;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+        if (__syncthreads_or((int)ncta != a.csize || (int)crank != me % a.csize)) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)DEV_LAUNCH);
+            return;
+        }
         const bool cluster0 = me < a.csize;  // cluster 0: CTAs 0 .. csize-1 of the 1-D grid
         bool dead = false;
         for (int s = 0; s < a.nseg; ++s) {
@@ -973,6 +985,14 @@ cudaError_t k_solve_attrs(size_t smem, int csize, int tile_ecap, int runs = 1) {
 template <typename T>
 cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t smem, int csize, cudaStream_t st,
                            int runs = 1) {
+    // SPTRSV_PROFILE_LAUNCH=1: launches with clusters go out without the cooperative attribute, for
+    // profilers that run cooperative launches without their cluster shape (the kernel detects that
+    // and stops with an error); the grid is sized from cluster occupancy either way, so every CTA of
+    // it is resident on an otherwise idle GPU
+    static const bool profile_launch = [] {
+        const char* e = std::getenv("SPTRSV_PROFILE_LAUNCH");
+        return e && e[0] == '1';
+    }();
     const int mode = k_mode(csize, a.tile_ecap, runs);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -980,15 +1000,18 @@ cudaError_t launch_k_solve(const SolveArgs<T>& a, int grid, int block, size_t sm
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    int na = 1;
+    int na = 0;
+    if (csize <= 1 || !profile_launch) {
+        attr[na].id = cudaLaunchAttributeCooperative;
+        attr[na].val.cooperative = 1;
+        ++na;
+    }
     if (csize > 1) {
-        attr[1].id = cudaLaunchAttributeClusterDimension;
-        attr[1].val.clusterDim.x = (unsigned)csize;
-        attr[1].val.clusterDim.y = 1;
-        attr[1].val.clusterDim.z = 1;
-        na = 2;
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = (unsigned)csize;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;

@@ -182,3 +182,28 @@ def test_shared_x_full_size_grid():
         s, x, ref, _ = solve_cluster(m, b, 16, system_kw=kw)
         assert s.refresh()["shared_x_levels"] > 0
         assert rel_l2(x, ref) <= TOL_F64
+
+
+def test_profile_launch_switch_keeps_cluster_shape():
+    """SPTRSV_PROFILE_LAUNCH=1 (read once per process, so in a child process): launches with clusters
+    go out without the cooperative attribute; the shared-x cluster solve still runs on its clusters
+    (the kernel checks its cluster shape on entry) and matches the oracle."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import numpy as np, torch\n"
+        "import oracle as O\n"
+        "from paper_2206_05843_gb300 import binding as B, synth as S\n"
+        "m = S.gen_laplacian(300); b = S.rhs_uniform(m.n, 1, 3)\n"
+        "M = B.Matrix.from_host(m); s = B.System(M, B.Levels(M)); s.tune(run_width=64); s.tune_cluster(16, 0)\n"
+        "x = s.solve(torch.from_numpy(b).cuda(), check_status=True).cpu().numpy()\n"
+        "ref = O.forward_subst(m.rowptr, m.colidx, m.vals, b)\n"
+        "info = s.refresh()\n"
+        "print(info['cluster'], info['shared_x_levels'], float(np.linalg.norm(x - ref) / np.linalg.norm(ref)))\n")
+    env = dict(os.environ, SPTRSV_PROFILE_LAUNCH="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    cl, shared, err = r.stdout.split()[-3:]
+    assert int(cl) == 16 and int(shared) > 0 and float(err) <= TOL_F64
