@@ -333,10 +333,16 @@ sptrsv_status sptrsv_system_reverse_rows(sptrsv_system* s, sptrsv_stream_t strea
  * ------------------------------------------------------------------------------- */
 
 /* Groups `count` systems (each solved for nrhs[i] right-hand sides, ld = n) into one
- * persistent launch captured in a CUDA graph: every CTA takes whole matrices, longest
- * critical path first, and crosses levels with CTA barriers.  Block size and lanes per
- * row are autotuned by timing candidate launches; the choice is cached by the batch
- * signature.  Systems must outlive the batch.  Synchronizes the stream. */
+ * persistent launch captured in a CUDA graph: every CTA takes whole work items, longest
+ * first, and crosses levels with CTA barriers.  A work item is a system with all its
+ * right-hand sides or a contiguous part of them (at most 8 parts), so that the parts of a heavy
+ * system run on several CTAs at once.  Three split policies: 0 splits a system whose float64
+ * work on one SM (about 0.25 ns x (stored entries + n) per right-hand side) exceeds both its
+ * critical path (about 250 ns per level) and an even share of the batch per SM; 1 and 2 cut
+ * into parts of at most 8 or 4 right-hand sides every system whose estimate exceeds 1.3 x the
+ * batch's longest critical path.  Split policy, block size and lanes per row are autotuned by
+ * timing candidate launches; the choice is cached by the batch signature.  Systems must
+ * outlive the batch.  Synchronizes the stream. */
 sptrsv_status sptrsv_batch_create(const sptrsv_system* const* systems_host, const int32_t* nrhs_host, int32_t count,
                                   sptrsv_batch** out, sptrsv_stream_t stream);
 
@@ -348,6 +354,8 @@ sptrsv_status sptrsv_batch_solve(sptrsv_batch* bt, const void* const* b_host, vo
 typedef struct {
     int32_t count, block, lanes_per_row, graph;
     double tuned_us;       /* best measured time of the autotuner */
+    int32_t items;         /* work items (systems, or parts of their right-hand sides) */
+    int32_t split_policy;  /* the autotuner's split policy: 0 by work, 1 and 2 parts of at most 8 and 4 */
 } sptrsv_batch_info;
 
 sptrsv_status sptrsv_batch_info_get(const sptrsv_batch* bt, sptrsv_batch_info* out_host);

@@ -77,7 +77,7 @@ class SystemInfo(C.Structure):
 
 class BatchInfo(C.Structure):
     _fields_ = [("count", C.c_int32), ("block", C.c_int32), ("lanes_per_row", C.c_int32), ("graph", C.c_int32),
-                ("tuned_us", C.c_double)]
+                ("tuned_us", C.c_double), ("items", C.c_int32), ("split_policy", C.c_int32)]
 
 
 _lib = None

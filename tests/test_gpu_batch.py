@@ -78,3 +78,25 @@ def test_batch_single_matrix_wide_levels():
     xs = bt.solve([torch.from_numpy(b).cuda()])
     torch.cuda.synchronize()
     assert rel_l2(xs[0].cpu().numpy(), O.forward_subst(m.rowptr, m.colidx, m.vals, b)) < TOL_F64
+
+
+def test_batch_splits_heavy_right_hand_sides():
+    """A banded matrix of 60,000 rows with 32 right-hand sides among small ones: its float64 work
+    outweighs its critical path, so its right-hand sides split into parts that run on several
+    CTAs (more work items than systems); every system and right-hand side matches the oracle, on
+    two graph replays."""
+    torch = torch_cuda()
+    items = S.gen_batch(count=10, base_seed=91, n_lo=1000, n_hi=6000, rhs_hi=3)
+    heavy = S.gen_banded_random(60_000, 5)
+    xt, b = S.rhs_from_xtrue(heavy, 32, 6)
+    items.insert(3, S.BatchItem(heavy, b, xt, 32, False, 0))
+    bt, mats, systems, keep = make_batch(items)
+    assert bt.info["items"] > bt.info["count"] == len(items)
+    for rep in range(2):
+        bs_host = [S.rhs_uniform(it.matrix.n, it.nrhs, 500 * rep + i) for i, it in enumerate(items)]
+        bs = [torch.from_numpy(b).to("cuda", dtype=torch.float32 if it.fp32 else torch.float64)
+              for b, it in zip(bs_host, items)]
+        xs = bt.solve(bs)
+        torch.cuda.synchronize()
+        bs_used = [b.astype(np.float32).astype(np.float64) if it.fp32 else b for b, it in zip(bs_host, items)]
+        check(items, mats, xs, bs_used)
