@@ -304,9 +304,9 @@ sptrsv_status sptrsv_system_tune_cluster(sptrsv_system* s, int32_t cluster, int6
                                          int32_t shared_x);
 
 /* Autotuner: times candidate solves (b = 0) over lanes per row, the widest level executed
- * inside a single-CTA run and the level-executor knobs (clusters of 16 or 8 CTAs or none,
- * tiles, then the widest cluster level and, for one right-hand side, the shared-x exchange
- * on and off), keeps the fastest for nrhs right-hand sides and caches the choice by the
+ * inside a single-CTA run and the level-executor knobs (clusters of 16 or 8 CTAs, with the
+ * shared-x exchange on and off for one right-hand side, or none, with or without tiles; then
+ * the widest cluster level), keeps the fastest for nrhs right-hand sides and caches the choice by the
  * system's signature (n, m, stored entries, nrhs, dtype).
  * *best_us_host (may be NULL) receives the best time.  Synchronizes the stream. */
 sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, double* best_us_host, sptrsv_stream_t stream);

@@ -570,24 +570,28 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         return SPTRSV_OK;
     };
     // lanes per row x widest single-CTA level x {no cluster with and without tiled wide levels,
-    // a cluster of 16 or 8 CTAs for mid-width levels}; then the widest cluster level for the best
-    const int cls[][3] = {{1, 0, 0}, {1, 0, 1}, {16, 16384, 1}, {8, 16384, 1}};
+    // a cluster of 16 or 8 CTAs for mid-width levels with and without the shared-x exchange};
+    // then the widest cluster level for the best
+    const int cls[][4] = {{1, 0, 0, 0}, {1, 0, 1, 0}, {16, 16384, 1, 0}, {8, 16384, 1, 0}, {16, 16384, 1, 1},
+                          {8, 16384, 1, 1}};
     for (int lpr : lprs) {
         for (int rw : widths) {
             if (rw == -2 && lpr != lprs[0]) continue;
             for (const auto& c : cls) {
                 if (rw == -2 && (c[0] != 1 || c[2] != 1)) continue;  // one launch per level: no clusters, no tiles
                 if (nrhs > 1 && c[0] == 1 && c[2] == 0) continue;   // tiles are for one right-hand side
+                if (nrhs > 1 && c[3] == 1) continue;                 // and the shared-x exchange
                 s->block = 512;
                 s->run_width = rw;
                 s->lpr = lpr;
                 s->cluster = c[0];
                 s->cluster_rows = c[1];
                 s->tiles = c[2];
+                s->shared_x = c[3];
                 double us = 0;
                 rc = time_current(&us);
                 if (rc != SPTRSV_OK) break;
-                if (us < best.us) best = TuneVal{512, rw, lpr, us, c[0], c[1], c[2]};
+                if (us < best.us) best = TuneVal{512, rw, lpr, us, c[0], c[1], c[2], c[3]};
             }
             if (rc != SPTRSV_OK) break;
         }
@@ -599,24 +603,14 @@ extern "C" sptrsv_status sptrsv_system_autotune(sptrsv_system* s, int32_t nrhs, 
         s->lpr = best.lpr;
         s->cluster = best.cluster;
         s->tiles = best.tiles;
+        s->shared_x = best.shared_x;
         for (int64_t rows : {(int64_t)4096, (int64_t)65536}) {
             s->cluster_rows = rows;
             double us = 0;
             rc = time_current(&us);
             if (rc != SPTRSV_OK) break;
-            if (us < best.us) best = TuneVal{best.block, best.run_width, best.lpr, us, best.cluster, rows, best.tiles};
-        }
-        // cluster levels of one right-hand side: also without the shared-memory exchange of x
-        if (rc == SPTRSV_OK && nrhs == 1) {
-            s->cluster_rows = best.cluster_rows;
-            s->shared_x = 1;
-            double us = 0;
-            rc = time_current(&us);
-            if (rc == SPTRSV_OK && us < best.us) {
-                best.us = us;
-                best.shared_x = 1;
-            }
-            s->shared_x = 0;
+            if (us < best.us)
+                best = TuneVal{best.block, best.run_width, best.lpr, us, best.cluster, rows, best.tiles, best.shared_x};
         }
     }
     cudaEventDestroy(e0);
