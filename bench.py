@@ -215,6 +215,27 @@ def cpu_oracle_time(m, b, seconds: float, steps: int | None = None):
     return statistics.median(t_all) * 1e6, count
 
 
+def cpu_oracle_preprocessing(m) -> dict:
+    """The serial CPU oracle's preprocessing of the same matrix, in ms on one host core: level
+    analysis, and the plan and rewrite of the naive strategy and of the row-capped walk (32 rows
+    per target), both under the 1.5 nnz cap -- the CPU counterpart of the GPU's analyse and
+    build times."""
+    import oracle as O
+    O.build()
+    out = {}
+    t = time.perf_counter()
+    level, nl = O.levels(m.rowptr, m.colidx)
+    out["oracle_cpu_levels_ms"] = round((time.perf_counter() - t) * 1e3, 1)
+    for name, kind, kw in (("naive", O.NAIVE, dict(cap=1.5)), ("rowcap", O.ROWCAP, dict(k=32, cap=1.5))):
+        t = time.perf_counter()
+        p = O.plan(m.rowptr, m.colidx, level, nl, kind, **kw)
+        out[f"oracle_cpu_plan_{name}_ms"] = round((time.perf_counter() - t) * 1e3, 1)
+        t = time.perf_counter()
+        O.rewrite(m.rowptr, m.colidx, m.vals, level, p.target)
+        out[f"oracle_cpu_rewrite_{name}_ms"] = round((time.perf_counter() - t) * 1e3, 1)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -556,14 +577,19 @@ def run_ours(args):
         for nm, kw in (("learned_model_only", dict(kind=B.LEARNED, cap=1.5, picker=B.Picker.load(PICKER_FILE),
                                                    model_only=True)),
                        ("naive", dict(kind=B.NAIVE, cap=1.5))):
+            torch.cuda.synchronize()
+            t_b = time.perf_counter()
             so = B.System(M, lv, **kw)
+            torch.cuda.synchronize()
+            build_ms = (time.perf_counter() - t_b) * 1e3
             so.autotune(nrhs)
             xo = torch.empty_like(bt)
             so.solve(bt, xo, check_status=True)
             us_o, _ = timed_us(torch, lambda: so.solve(bt, xo), args.steps, args.warmup, flush, stream)
             so.status()
             io = so.refresh()
-            others[nm] = {"us": round(us_o, 3), "levels": int(io["m"]), "rows_moved": int(io["rows_moved"]),
+            others[nm] = {"us": round(us_o, 3), "build_ms": round(build_ms, 1), "levels": int(io["m"]),
+                          "rows_moved": int(io["rows_moved"]),
                           "stored_nnz_ratio": round(io["stored_nnz"] / io["nnz_l"], 4),
                           "rel_err_vs_x_true": float(np.linalg.norm(xo.cpu().numpy() - xt_true) /
                                                      np.linalg.norm(xt_true)) if xt_true is not None else None}
@@ -631,8 +657,11 @@ def run_ours(args):
     crit["plain"] = {"floor_us": crit_pl["floor_us"], "achieved_us": round(us_plain, 1),
                      "frac": round(crit_pl["floor_us"] / us_plain, 4) if us_plain > 0 else None}
     cpu = None
+    cpu_prep = {}
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
         us_cpu, count = cpu_oracle_time(m, b, args.cpu_seconds)
+        if args.workload == "c1":
+            cpu_prep = cpu_oracle_preprocessing(m)
         cpu = {"value": round(us_cpu, 1), "unit": "us", "cores": 1, "kind": "oracle",
                "sample": f"{count} whole serial solves of the same workload (median), {os.cpu_count()} host cores present"}
     line = {
@@ -675,6 +704,8 @@ def run_ours(args):
             **{f"{k}_us": v["us"] for k, v in others.items()},
             **({"candidate_us_model_naive_rowcap_plain": [round(v, 1) for v in info_rw["candidate_us"]]}
                if used == "learned" else {}),
+            **({"naive_build_ms": others["naive"]["build_ms"]} if "naive" in others else {}),
+            **cpu_prep,
             **flat_extras(extras),
         },
         "roofline": {"bound": "hbm", "achieved": round(gbs_rw, 2), "peak": peak, "unit": "GB/s",

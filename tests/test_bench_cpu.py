@@ -63,3 +63,14 @@ def test_rel_residual_of_an_exact_and_a_perturbed_solution():
 def test_flat_extras_keeps_time_and_fraction_or_the_error():
     ex = {"w2": {"us": 200.0, "hbm_frac": 0.5, "gbs": 3000.0}, "c3": {"error": "RuntimeError: x"}}
     assert bench.flat_extras(ex) == {"w2_us": 200.0, "w2_hbm_frac": 0.5, "c3_error": "RuntimeError: x"}
+
+
+def test_cpu_oracle_preprocessing_times_every_step():
+    """The bench's CPU preprocessing baseline times the oracle's level analysis and the naive and
+    row-capped plans and rewrites on the workload it is given (a small skewed matrix here)."""
+    from paper_2206_05843_gb300 import synth as S
+    m, _, _ = S.gen_config("c1", scale=0.01)
+    out = bench.cpu_oracle_preprocessing(m)
+    assert set(out) == {"oracle_cpu_levels_ms", "oracle_cpu_plan_naive_ms", "oracle_cpu_rewrite_naive_ms",
+                        "oracle_cpu_plan_rowcap_ms", "oracle_cpu_rewrite_rowcap_ms"}
+    assert all(isinstance(v, float) and v >= 0 for v in out.values())
