@@ -86,6 +86,45 @@ __device__ int sort_unique(int32_t* a, int len) {
     return w;
 }
 
+// entries of one candidate set the warp sorts together in shared memory
+constexpr int WALK_SORT_CAP = 512;
+
+// The warp sorts and de-duplicates a[0, len) (global memory) together: each lane ranks its entries
+// against all the others in shared memory -- an entry is kept when no earlier entry has its value,
+// and goes to the place given by the number of distinct smaller values.  Returns the new length (on
+// every lane).  A longer set is sorted by lane 0 alone.  Called by the whole warp.
+__device__ int warp_sort_unique(int32_t* a, int len, int32_t* sv, int32_t* sk) {
+    const int lane = threadIdx.x & 31;
+    if (len > WALK_SORT_CAP) {
+        int out = 0;
+        if (lane == 0) out = sort_unique(a, len);
+        __syncwarp();
+        return __shfl_sync(0xffffffffu, out, 0);
+    }
+    for (int i = lane; i < len; i += 32) sv[i] = a[i];
+    __syncwarp();
+    for (int i = lane; i < len; i += 32) {
+        const int32_t v = sv[i];
+        int dup = 0;
+        for (int k = 0; k < i; ++k) dup |= sv[k] == v;
+        sk[i] = !dup;
+    }
+    __syncwarp();
+    int kept = 0;
+    for (int i = lane; i < len; i += 32) {
+        if (!sk[i]) continue;
+        const int32_t v = sv[i];
+        int pos = 0;
+        for (int k = 0; k < len; ++k) pos += (sk[k] && sv[k] < v) ? 1 : 0;
+        a[pos] = v;
+        ++kept;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    __syncwarp();
+    return kept;
+}
+
 struct WalkArgs {
     int64_t n, m, nnzL;
     const int32_t* rowptr;
@@ -118,7 +157,10 @@ struct WalkArgs {
 // walk).  A range only rewrites rows of its own levels, and substitution never reaches below a
 // target, so it reads nothing another range writes that could change its decisions: a dependency
 // in an earlier range sits on a level below the range's targets whatever its own range did.
+// Candidate sets of a chunk of at most 4 rows (thin levels: mostly 1 or 2) are sorted by the whole
+// warp, one row after the other (warp_sort_unique); larger chunks sort a row per lane.
 __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
+    extern __shared__ int32_t walk_smem[];  // 2 x WALK_SORT_CAP: values and keep flags
     const int lane = threadIdx.x;
     const int w = blockIdx.x, P = gridDim.x;
     const int64_t s_begin = a.m * w / P, s_end = a.m * (w + 1) / P;
@@ -147,6 +189,8 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
         }
         const int64_t A = a.lptr[s], Bn = a.lptr[s + 1];
         for (int64_t base = A; base < Bn; base += 32) {
+            const int nvalid = (int)(Bn - base < 32 ? Bn - base : 32);
+            const bool coop = nvalid <= 4;  // warp-uniform
             const int64_t idx = base + lane;
             const bool valid = idx < Bn;
             const int32_t r = valid ? a.lrows[idx] : 0;
@@ -192,8 +236,24 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
                     }
                 }
                 Ep[ne++] = r;
-                nd = sort_unique(Dp, nd);
-                ne = sort_unique(Ep, ne);
+                if (!coop) {
+                    nd = sort_unique(Dp, nd);
+                    ne = sort_unique(Ep, ne);
+                }
+            }
+            if (coop) {
+                __syncwarp();  // every lane's concatenated sets are in the pool
+                for (int L = 0; L < nvalid; ++L) {
+                    int32_t* dl = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)Dp, L);
+                    int32_t* el = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)Ep, L);
+                    const int dn = __shfl_sync(0xffffffffu, nd, L), en = __shfl_sync(0xffffffffu, ne, L);
+                    const int dn2 = warp_sort_unique(dl, dn, walk_smem, walk_smem + WALK_SORT_CAP);
+                    const int en2 = warp_sort_unique(el, en, walk_smem, walk_smem + WALK_SORT_CAP);
+                    if (lane == L) {
+                        nd = dn2;
+                        ne = en2;
+                    }
+                }
             }
             const int64_t c = valid ? (a.inj ? a.inj[r] : 2 * (int64_t)nd) : 0;
             const int64_t growth = valid ? (int64_t)nd + ne - (q1 - q0) : 0;
@@ -209,7 +269,6 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
                               (limit == INT64_MAX || stored + pg <= limit) && lane < first_bad;
             const unsigned failmask = __ballot_sync(0xffffffffu, valid && !pass);
             const int first = failmask ? __ffs(failmask) - 1 : 32;
-            const int nvalid = (int)(Bn - base < 32 ? Bn - base : 32);
             const int acc_n = min(first, nvalid);
             if (lane < acc_n) {
                 a.target[r] = t;
@@ -580,7 +639,7 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
         a.pool_cap = cap_pool;
         a.info = info.as<int64_t>();
         a.status = status.as<int>();
-        k_plan_walk<<<parts, 32, 0, st>>>(a);
+        k_plan_walk<<<parts, 32, 2 * WALK_SORT_CAP * sizeof(int32_t), st>>>(a);
         SP_CUDA(cudaGetLastError());
         int hs = 0;
         std::vector<int64_t> hi((size_t)parts * 3);
