@@ -80,3 +80,24 @@ def test_noalloc_float32_and_one_launch_per_level():
             s.solve_noalloc(b, x)
             s.status()
             assert rel_l2(x.cpu().numpy(), ref.cpu().numpy()) <= TOL_F32
+
+
+def test_noalloc_cluster_levels_with_shared_x():
+    """A schedule whose mid-width levels run on a 16-CTA cluster and read the previous level's x from
+    the cluster's shared memory: the entry point launches the same kernel; two calls in a row match
+    the regular solve."""
+    torch = torch_cuda()
+    m = S.gen_laplacian(300)
+    M = B.Matrix.from_host(m)
+    s = B.System(M, B.Levels(M))
+    s.tune(run_width=64)
+    s.tune_cluster(16, 0)
+    x = None
+    for seed in (6, 7):
+        b = torch.from_numpy(S.rhs_uniform(m.n, 1, seed)[0]).cuda()
+        ref = s.solve(b, check_status=True).clone()
+        assert s.refresh()["shared_x_levels"] > 0
+        x = torch.empty_like(b) if x is None else x
+        s.solve_noalloc(b, x)
+        s.status()
+        assert rel_l2(x.cpu().numpy(), ref.cpu().numpy()) <= TOL_F64
