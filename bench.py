@@ -197,6 +197,18 @@ def alg_bytes(info: dict, n: int, nrhs: int, v: int = 8) -> int:
 # the reference arm: the CPU oracle
 # ------------------------------------------------------------------------------------
 
+def fp64_ops(info: dict, nrhs: int) -> int:
+    """float64 operations of one solve: per right-hand side one FMA per stored coefficient and per E
+    entry, and the 1/L_rr product of every row."""
+    return (int(info["nnz_c"]) + int(info["nnz_e"]) + int(info["n"])) * nrhs
+
+
+def fp64_peak(sms: int, sm_mhz: float) -> float:
+    """float64 operations per second at full issue: an SM runs four float64 warp instructions of 64
+    cycles at a time, 2 lane operations per cycle."""
+    return sms * 2.0 * sm_mhz * 1e6
+
+
 def cpu_oracle_time(m, b, seconds: float, steps: int | None = None):
     import oracle as O
     O.build()
@@ -393,7 +405,7 @@ def rel_residual(m, x, b) -> float:
     return out
 
 
-def measure_single(torch, B, m, b, xt, kw, steps, warmup, flush, stream, peak):
+def measure_single(torch, B, m, b, xt, kw, steps, warmup, flush, stream, peak, fpeak=None):
     """One system of one workload: autotuned for its right-hand sides, mean solve time with L2
     flushed, algorithmic bytes, GB/s and the fraction of the HBM peak, error against x_true
     (or the relative residual when b is not built from a known x)."""
@@ -413,6 +425,8 @@ def measure_single(torch, B, m, b, xt, kw, steps, warmup, flush, stream, peak):
     gbs = by / (us * 1e-6) / 1e9
     out = {"us": round(us, 2), "median_us": round(med, 2), "levels": int(info["m"]), "alg_bytes": by,
            "gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4), "launches": int(info["launches"])}
+    if fpeak:
+        out["fp64_frac"] = round(fp64_ops(info, nrhs) / (us * 1e-6) / fpeak, 4)
     if xt is not None:
         out["rel_err_vs_x_true"] = float(np.linalg.norm(xx - xt) / np.linalg.norm(xt))
     else:
@@ -420,7 +434,7 @@ def measure_single(torch, B, m, b, xt, kw, steps, warmup, flush, stream, peak):
     return out
 
 
-def measure_batch(torch, B, steps, warmup, flush, stream, peak, rank=0, world=1):
+def measure_batch(torch, B, steps, warmup, flush, stream, peak, rank=0, world=1, fpeak=None):
     """The 256-matrix batch (n log-uniform in [1,000, 65,536], 1..32 right-hand sides, float64
     and float32 values alternating): one graph replay per step.  With several ranks every rank
     takes its share of the matrices (paper_2206_05843_gb300.shard; no collective)."""
@@ -430,14 +444,16 @@ def measure_batch(torch, B, steps, warmup, flush, stream, peak, rank=0, world=1)
     if world > 1:
         mine = shard.shard_batch([shard.item_cost(it.matrix.nnz, it.nrhs) for it in items], world)[rank]
         items = [items[i] for i in mine]
-    keep, systems, by = [], [], 0
+    keep, systems, by, ops = [], [], 0, 0
     for it in items:
         mt = it.matrix.astype(np.float32) if it.fp32 else it.matrix
         M = B.Matrix.from_host(mt)
         s = B.System(M, B.Levels(M))
         keep.append((mt, M))
         systems.append(s)
-        by += alg_bytes(s.refresh(), mt.n, it.nrhs, 4 if it.fp32 else 8)
+        inf = s.refresh()
+        by += alg_bytes(inf, mt.n, it.nrhs, 4 if it.fp32 else 8)
+        ops += fp64_ops(inf, it.nrhs)
     bt = B.Batch(systems, [it.nrhs for it in items])
     bs = [torch.from_numpy(it.b).to("cuda", dtype=torch.float32 if it.fp32 else torch.float64) for it in items]
     xs = [torch.empty_like(b_) for b_ in bs]
@@ -454,25 +470,32 @@ def measure_batch(torch, B, steps, warmup, flush, stream, peak, rank=0, world=1)
     for s in systems:
         s.status()
     gbs = by / (us * 1e-6) / 1e9
-    return {"us": round(us, 2), "median_us": round(med, 2), "matrices": len(items),
-            "rows": int(sum(it.matrix.n for it in items)), "alg_bytes": by, "gbs": round(gbs, 1),
-            "hbm_frac": round(gbs / peak, 4), "block": int(bt.info["block"]),
-            "rel_residual_f64_max": err64, "rel_residual_f32_max": err32}
+    out = {"us": round(us, 2), "median_us": round(med, 2), "matrices": len(items),
+           "rows": int(sum(it.matrix.n for it in items)), "alg_bytes": by, "gbs": round(gbs, 1),
+           "hbm_frac": round(gbs / peak, 4), "block": int(bt.info["block"]), "work_items": int(bt.info["items"]),
+           "split_policy": int(bt.info["split_policy"]),
+           "rel_residual_f64_max": err64, "rel_residual_f32_max": err32}
+    if fpeak:  # float32 items counted as float64 operations: an upper bound of the issue they need
+        out["fp64_frac"] = round(ops / (us * 1e-6) / fpeak, 4)
+    return out
 
 
 def flat_extras(extras: dict) -> dict:
-    """Scalar summary of the extra workloads for the line's config: time and HBM fraction."""
+    """Scalar summary of the extra workloads for the line's config: time, HBM fraction and, where
+    measured, the fraction of full float64 issue."""
     out = {}
     for k, v in extras.items():
         if "us" in v:
             out[f"{k}_us"] = v["us"]
             out[f"{k}_hbm_frac"] = v["hbm_frac"]
+            if "fp64_frac" in v:
+                out[f"{k}_fp64_frac"] = v["fp64_frac"]
         else:
             out[f"{k}_error"] = v.get("error", "?")
     return out
 
 
-def measure_extras(torch, B, names, steps, warmup, flush, stream, peak, rank=0, world=1):
+def measure_extras(torch, B, names, steps, warmup, flush, stream, peak, rank=0, world=1, fpeak=None):
     """The extra workloads; with several ranks the single matrices run as replicas and the batch is
     shared out, and every time is the maximum over ranks."""
     from paper_2206_05843_gb300 import synth as S
@@ -482,11 +505,11 @@ def measure_extras(torch, B, names, steps, warmup, flush, stream, peak, rank=0, 
         try:
             if name in ("w1", "w2"):
                 m, b, xt = S.gen_config(name)
-                out[name] = measure_single(torch, B, m, b, xt, {}, steps, warmup, flush, stream, peak)
+                out[name] = measure_single(torch, B, m, b, xt, {}, steps, warmup, flush, stream, peak, fpeak)
             elif name == "w1r16":
                 m, _, _ = S.gen_config("w1")
                 xt, b = S.rhs_from_xtrue(m, 16, 1)
-                out[name] = measure_single(torch, B, m, b, xt, {}, steps, warmup, flush, stream, peak)
+                out[name] = measure_single(torch, B, m, b, xt, {}, steps, warmup, flush, stream, peak, fpeak)
             elif name == "c2":
                 m, _, _ = S.gen_config("c2")
                 for r in (1, 16):
@@ -494,9 +517,9 @@ def measure_extras(torch, B, names, steps, warmup, flush, stream, peak, rank=0, 
                     for k in (0, 1, 2, 4):
                         kw = {} if k == 0 else dict(kind=B.DEPTH_K, k=k)
                         out[f"c2_r{r}_k{k}"] = measure_single(torch, B, m, b, None, kw, steps, warmup, flush,
-                                                              stream, peak)
+                                                              stream, peak, fpeak)
             elif name == "c3":
-                out[name] = measure_batch(torch, B, steps, warmup, flush, stream, peak, rank, world)
+                out[name] = measure_batch(torch, B, steps, warmup, flush, stream, peak, rank, world, fpeak)
                 if world > 1:
                     out[name]["ranks"] = world
                     out[name]["note"] = "us: maximum over ranks; matrices, rows, alg_bytes, gbs, hbm_frac: rank 0's share"
@@ -625,7 +648,10 @@ def run_ours(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     names = [w for w in args.extra.split(",") if w and w != "none"] if args.workload == "c1" else []
-    extras = measure_extras(torch, B, names, args.steps, args.warmup, flush, stream, peak, rank, world)
+    # full float64 issue at the clock sampled during the headline's timed region
+    clk_mhz = float(clk.get("sm_mhz") or 0) if isinstance(clk, dict) else 0.0
+    fpeak = fp64_peak(torch.cuda.get_device_properties(0).multi_processor_count, clk_mhz if clk_mhz > 0 else 2070.0)
+    extras = measure_extras(torch, B, names, args.steps, args.warmup, flush, stream, peak, rank, world, fpeak)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()

@@ -61,8 +61,23 @@ def test_rel_residual_of_an_exact_and_a_perturbed_solution():
 
 
 def test_flat_extras_keeps_time_and_fraction_or_the_error():
-    ex = {"w2": {"us": 200.0, "hbm_frac": 0.5, "gbs": 3000.0}, "c3": {"error": "RuntimeError: x"}}
-    assert bench.flat_extras(ex) == {"w2_us": 200.0, "w2_hbm_frac": 0.5, "c3_error": "RuntimeError: x"}
+    ex = {"w2": {"us": 200.0, "hbm_frac": 0.5, "gbs": 3000.0}, "c3": {"error": "RuntimeError: x"},
+          "w1r16": {"us": 955.0, "hbm_frac": 0.19, "fp64_frac": 0.56}}
+    assert bench.flat_extras(ex) == {"w2_us": 200.0, "w2_hbm_frac": 0.5, "c3_error": "RuntimeError: x",
+                                     "w1r16_us": 955.0, "w1r16_hbm_frac": 0.19, "w1r16_fp64_frac": 0.56}
+
+
+def test_fp64_issue_bound_of_a_known_workload():
+    """float64 operations per solve and the full-issue rate: n = 4,194,304 rows with 4 off-diagonal
+    entries in all but 8,192 rows and 16 right-hand sides need about 335 M operations, 533 us at
+    152 SMs x 2 operations a cycle at 2,070 MHz."""
+    n = 2048 * 2048
+    nnz_c = 4 * n - 4 * 2048
+    ops = bench.fp64_ops({"nnz_c": nnz_c, "nnz_e": 0, "n": n}, 16)
+    assert ops == (nnz_c + n) * 16
+    peak = bench.fp64_peak(152, 2070.0)
+    assert peak == 152 * 2 * 2070e6
+    assert 520e-6 < ops / peak < 540e-6
 
 
 def test_cpu_oracle_preprocessing_times_every_step():
