@@ -89,20 +89,13 @@ __device__ int sort_unique(int32_t* a, int len) {
 // entries of one candidate set the warp sorts together in shared memory
 constexpr int WALK_SORT_CAP = 512;
 
-// The warp sorts and de-duplicates a[0, len) (global memory) together: each lane ranks its entries
-// against all the others in shared memory -- an entry is kept when no earlier entry has its value,
-// and goes to the place given by the number of distinct smaller values.  Returns the new length (on
-// every lane).  A longer set is sorted by lane 0 alone.  Called by the whole warp.
-__device__ int warp_sort_unique(int32_t* a, int len, int32_t* sv, int32_t* sk) {
+// The warp sorts and de-duplicates len <= WALK_SORT_CAP values in shared memory sv[0, len) together:
+// each lane ranks its entries against all the others -- an entry is kept when no earlier entry has its
+// value, and goes to the place given by the number of distinct smaller values -- and the sorted
+// distinct values go to dst (global memory).  Returns the new length on every lane.  Called by the
+// whole warp.
+__device__ int warp_sort_unique_smem(const int32_t* sv, int len, int32_t* sk, int32_t* dst) {
     const int lane = threadIdx.x & 31;
-    if (len > WALK_SORT_CAP) {
-        int out = 0;
-        if (lane == 0) out = sort_unique(a, len);
-        __syncwarp();
-        return __shfl_sync(0xffffffffu, out, 0);
-    }
-    for (int i = lane; i < len; i += 32) sv[i] = a[i];
-    __syncwarp();
     for (int i = lane; i < len; i += 32) {
         const int32_t v = sv[i];
         int dup = 0;
@@ -116,7 +109,7 @@ __device__ int warp_sort_unique(int32_t* a, int len, int32_t* sv, int32_t* sk) {
         const int32_t v = sv[i];
         int pos = 0;
         for (int k = 0; k < len; ++k) pos += (sk[k] && sv[k] < v) ? 1 : 0;
-        a[pos] = v;
+        dst[pos] = v;
         ++kept;
     }
 #pragma unroll
@@ -157,10 +150,10 @@ struct WalkArgs {
 // walk).  A range only rewrites rows of its own levels, and substitution never reaches below a
 // target, so it reads nothing another range writes that could change its decisions: a dependency
 // in an earlier range sits on a level below the range's targets whatever its own range did.
-// Candidate sets of a chunk of at most 4 rows (thin levels: mostly 1 or 2) are sorted by the whole
-// warp, one row after the other (warp_sort_unique); larger chunks sort a row per lane.
+// Candidate sets of a chunk of at most 4 rows (thin levels: mostly 1 or 2) are gathered and sorted by
+// the whole warp, one row after the other (warp_sort_unique_smem); larger chunks take a row per lane.
 __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
-    extern __shared__ int32_t walk_smem[];  // 2 x WALK_SORT_CAP: values and keep flags
+    extern __shared__ int32_t walk_smem[];  // 3 x WALK_SORT_CAP: D values, E values, keep flags
     const int lane = threadIdx.x;
     const int w = blockIdx.x, P = gridDim.x;
     const int64_t s_begin = a.m * w / P, s_end = a.m * (w + 1) / P;
@@ -218,7 +211,7 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
             int32_t* Dp = pool + top + off;
             int32_t* Ep = Dp + ubD;
             int nd = 0, ne = 0;
-            if (valid) {
+            if (valid && !coop) {
                 for (int64_t q = q0; q < q1; ++q) {
                     const int32_t j = a.colidx[q];
                     if (a.target[j] >= t) {
@@ -236,22 +229,82 @@ __global__ void __launch_bounds__(32) k_plan_walk(WalkArgs a) {
                     }
                 }
                 Ep[ne++] = r;
-                if (!coop) {
-                    nd = sort_unique(Dp, nd);
-                    ne = sort_unique(Ep, ne);
-                }
+                nd = sort_unique(Dp, nd);
+                ne = sort_unique(Ep, ne);
             }
             if (coop) {
-                __syncwarp();  // every lane's concatenated sets are in the pool
+                // rows one after the other, each gathered by the whole warp: dependency by dependency,
+                // the same lists in the same order as the lane-per-row concatenation above, into shared
+                // memory (sets of at most WALK_SORT_CAP entries; a longer one is gathered by its lane into
+                // the pool), then sorted and de-duplicated into the pool
+                int32_t* sD = walk_smem;
+                int32_t* sE = walk_smem + WALK_SORT_CAP;
+                int32_t* sK = walk_smem + 2 * WALK_SORT_CAP;
                 for (int L = 0; L < nvalid; ++L) {
                     int32_t* dl = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)Dp, L);
                     int32_t* el = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)Ep, L);
-                    const int dn = __shfl_sync(0xffffffffu, nd, L), en = __shfl_sync(0xffffffffu, ne, L);
-                    const int dn2 = warp_sort_unique(dl, dn, walk_smem, walk_smem + WALK_SORT_CAP);
-                    const int en2 = warp_sort_unique(el, en, walk_smem, walk_smem + WALK_SORT_CAP);
+                    const int32_t rl = __shfl_sync(0xffffffffu, r, L);
+                    const int64_t a0 = __shfl_sync(0xffffffffu, q0, L), a1 = __shfl_sync(0xffffffffu, q1, L);
+                    const int64_t uD = __shfl_sync(0xffffffffu, ubD, L), uE = __shfl_sync(0xffffffffu, ubE, L);
+                    int dn = 0, en = 0;
+                    if (uD <= WALK_SORT_CAP && uE <= WALK_SORT_CAP) {
+                        for (int64_t q = a0; q < a1; ++q) {
+                            const int32_t j = a.colidx[q];
+                            if (a.target[j] >= t) {
+                                if (a.level[j] != t) {
+                                    const int64_t o = a.d_off[j], oe = a.e_off[j];
+                                    const int ld = a.d_len[j], le = a.e_len[j];
+                                    for (int u = lane; u < ld; u += 32) sD[dn + u] = pool[o + u];
+                                    for (int u = lane; u < le; u += 32) sE[en + u] = pool[oe + u];
+                                    dn += ld;
+                                    en += le;
+                                } else {
+                                    const int64_t b0 = a.rowptr[j], b1 = (int64_t)a.rowptr[j + 1] - 1;
+                                    for (int64_t u = b0 + lane; u < b1; u += 32) sD[dn + (int)(u - b0)] = a.colidx[u];
+                                    dn += (int)(b1 - b0);
+                                    if (lane == 0) sE[en] = j;
+                                    ++en;
+                                }
+                            } else {
+                                if (lane == 0) sD[dn] = j;
+                                ++dn;
+                            }
+                        }
+                        if (lane == 0) sE[en] = rl;
+                        ++en;
+                        __syncwarp();
+                        dn = warp_sort_unique_smem(sD, dn, sK, dl);
+                        en = warp_sort_unique_smem(sE, en, sK, el);
+                    } else {
+                        if (lane == L) {
+                            for (int64_t q = a0; q < a1; ++q) {
+                                const int32_t j = a.colidx[q];
+                                if (a.target[j] >= t) {
+                                    if (a.level[j] != t) {
+                                        const int64_t o = a.d_off[j];
+                                        for (int u = 0; u < a.d_len[j]; ++u) dl[dn++] = pool[o + u];
+                                        const int64_t oe = a.e_off[j];
+                                        for (int u = 0; u < a.e_len[j]; ++u) el[en++] = pool[oe + u];
+                                    } else {
+                                        for (int64_t u = a.rowptr[j]; u < (int64_t)a.rowptr[j + 1] - 1; ++u)
+                                            dl[dn++] = a.colidx[u];
+                                        el[en++] = j;
+                                    }
+                                } else {
+                                    dl[dn++] = j;
+                                }
+                            }
+                            el[en++] = rl;
+                            dn = sort_unique(dl, dn);
+                            en = sort_unique(el, en);
+                        }
+                        __syncwarp();
+                        dn = __shfl_sync(0xffffffffu, dn, L);
+                        en = __shfl_sync(0xffffffffu, en, L);
+                    }
                     if (lane == L) {
-                        nd = dn2;
-                        ne = en2;
+                        nd = dn;
+                        ne = en;
                     }
                 }
             }
@@ -639,7 +692,7 @@ sptrsv_status plan_targets(const sptrsv_csr* L, const Levels& lv, int kind, int 
         a.pool_cap = cap_pool;
         a.info = info.as<int64_t>();
         a.status = status.as<int>();
-        k_plan_walk<<<parts, 32, 2 * WALK_SORT_CAP * sizeof(int32_t), st>>>(a);
+        k_plan_walk<<<parts, 32, 3 * WALK_SORT_CAP * sizeof(int32_t), st>>>(a);
         SP_CUDA(cudaGetLastError());
         int hs = 0;
         std::vector<int64_t> hi((size_t)parts * 3);
